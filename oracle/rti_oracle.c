@@ -1,0 +1,583 @@
+/*
+ * rti_oracle.c -- plain FP64 CPU oracle of the RTi / TUNAMI-N2 time step.
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, the smoke check and the benchmark's CPU
+ * baseline). Slow on purpose: one plain loop per rule, no blocking, no fusion,
+ * no reordering beyond what the rules below state. Build with
+ * -ffp-contract=off so that no multiply-add is fused.
+ *
+ * Source: Takahashi et al., "Modernizing an Operational Real-time Tsunami
+ * Simulator to Support Diverse Hardware Platforms".
+ *   Eq. 1 (Sec. II-A)  continuity  d(eta)/dt + dM/dx + dN/dy = 0
+ *   Eq. 2, Eq. 3       momentum with advection, g D grad(eta) and Manning friction
+ *                      g n^2 D^(-7/3) M sqrt(M^2+N^2); D = h + eta
+ *   Eq. 4              CFL  dx/dt >= sqrt(2 g h_max)
+ *   Sec. II-A          leap-frog in time, staggered grid, 1:3 inclusive nesting
+ *   Sec. IV-A, Fig. 2  loop order: mass, child->parent eta, momentum,
+ *                      parent->child fluxes, output update, buffer swap
+ *   Sec. IV-C-2, Listing 5  child->parent eta = (sum of a 3x3 child patch) * (1/9)
+ *   Sec. V-A           one dt on all levels
+ * The paper gives no discrete stencil. The readings used here:
+ *   R1  mass: eta1 = eta - ((dt/dx)(Me - Mw) + (dt/dx)(Nn - Ns)), every cell.
+ *   R2  x-momentum at interior faces: D_f = (hL+hR)/2 + (etaL+etaR)/2 from the new
+ *       eta; first-order upwind advection on the sign of M (x) and of the 4-point mean
+ *       N (y), each flux over its own face depth; centred when the sign is zero;
+ *       dropped when a face it needs is a block-boundary face or has D <= dry_eps;
+ *       pressure g D_f (dt/dx)(etaR - etaL); semi-implicit Manning friction
+ *       F = (dt/2) g n_f^2 sqrt(M^2 + Nbar^2) / (D_f^2 cbrt(D_f)), n_f = max(nL, nR);
+ *       M1 = ((1 - F) M - dt Adv - P) / (1 + F).
+ *   R3  y-momentum: R2 with x and y exchanged, same operation order.
+ *   R4  wet/dry front: a cell is wet when h + eta > dry_eps. Both wet: R2. One wet and
+ *       its level above the dry cell's ground: D_f = eta_wet + h_dry, gradient against
+ *       the dry ground level, no advection. Otherwise, or when D_f <= dry_eps, zero.
+ *   R5  clip after R1: if h + eta < 0 then eta = -h; the added volume is counted.
+ *   R6  root-block edges: wall = zero flux; radiation = outward sqrt(g max(h,0)) eta of
+ *       the adjacent cell when that cell is wet, else zero.
+ *   R7  coarse->fine: each child edge face takes the parent flux on the coarse face it
+ *       lies on, linearly interpolated along the edge (weights 2/3, 1/3 at the outer fine
+ *       faces, neighbour clamped at the segment ends); no time interpolation.
+ *   R8  fine->coarse: parent cells on the inner ring of the child footprint take the
+ *       Listing 5 mean of their 3x3 child cells (x outer, y inner, FP64 sum, times 1/9).
+ *       Only wet child cells enter the mean (sum times 1/count; all nine wet gives the
+ *       listing's formula exactly); the result is floored at the parent's ground level
+ *       -h; a patch with no wet cell leaves the parent's own value. Averaging dry land
+ *       levels into a sea cell would break the lake at rest.
+ *   R9  after R8: on wet cells, etamax = max(etamax, eta); the arrival step is recorded
+ *       when etamax first reaches the threshold (>=).
+ *   R10 initial state: eta0 = max(dz, -h) on sea cells, -h on land, fluxes zero.
+ */
+#include "rti_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NEVER_WET (-1.0e30)
+
+typedef struct {
+  orc_block d;
+  int nx, ny;
+  double dx, dtdx;
+  double* h;    /* nx*ny */
+  double* n;    /* nx*ny, Manning n (input floats, exactly widened) */
+  double* eta;  /* eta^n */
+  double* eta1; /* eta^{n+1} */
+  double* M;    /* ny*(nx+1) */
+  double* M1;
+  double* N;    /* (ny+1)*nx */
+  double* N1;
+  double* emax;
+  long* arr; /* arrival step, -1 if never */
+  double outflow, clip, ring;
+} oblk;
+
+struct orc_state {
+  int nb;
+  oblk* b;
+  orc_params p;
+  long step;
+};
+
+/* index helpers: cell (i,j), x-face (f,j), y-face (i,g) */
+#define C(b, i, j) ((size_t)(j) * (size_t)(b)->nx + (size_t)(i))
+#define FX(b, f, j) ((size_t)(j) * (size_t)((b)->nx + 1) + (size_t)(f))
+#define FY(b, i, g) ((size_t)(g) * (size_t)(b)->nx + (size_t)(i))
+
+static void free_blk(oblk* b) {
+  free(b->h); free(b->n); free(b->eta); free(b->eta1); free(b->M); free(b->M1);
+  free(b->N); free(b->N1); free(b->emax); free(b->arr);
+}
+
+void orc_destroy(orc_state* s) {
+  if (!s) return;
+  for (int k = 0; k < s->nb; ++k) free_blk(&s->b[k]);
+  free(s->b);
+  free(s);
+}
+
+static int check_blocks(const orc_block* bl, int nb, const double* const* bathy,
+                        const orc_params* p) {
+  for (int k = 0; k < nb; ++k) {
+    const orc_block* d = &bl[k];
+    if (d->nx < 3 || d->ny < 3 || !(d->dx > 0)) return ORC_ERR_INVALID_ARG;
+    /* Eq. 4: dx / dt >= sqrt(2 g h_max) on every block */
+    double hmax = 0;
+    for (size_t c = 0; c < (size_t)d->nx * d->ny; ++c)
+      if (bathy[k][c] > hmax) hmax = bathy[k][c];
+    if (d->dx / p->dt < sqrt(2.0 * p->g * hmax)) return ORC_ERR_CFL;
+    if (d->parent < 0) {
+      if (d->level != 1) return ORC_ERR_NESTING;
+      continue;
+    }
+    if (d->parent >= k) return ORC_ERR_NESTING; /* parents come first */
+    const orc_block* P = &bl[d->parent];
+    if (d->level != P->level + 1) return ORC_ERR_NESTING;
+    if (d->nx % 3 || d->ny % 3) return ORC_ERR_NESTING;
+    if (fabs(d->dx * 3.0 - P->dx) > 1e-9 * P->dx) return ORC_ERR_NESTING;
+    /* inclusive nesting with a 3-cell margin inside the parent */
+    if (d->i0 < 3 || d->j0 < 3 || d->i0 + d->nx / 3 > P->nx - 3 || d->j0 + d->ny / 3 > P->ny - 3)
+      return ORC_ERR_NESTING;
+    for (int q = 0; q < k; ++q) { /* siblings may touch but not overlap */
+      const orc_block* o = &bl[q];
+      if (o->parent != d->parent) continue;
+      int ox = d->i0 < o->i0 + o->nx / 3 && o->i0 < d->i0 + d->nx / 3;
+      int oy = d->j0 < o->j0 + o->ny / 3 && o->j0 < d->j0 + d->ny / 3;
+      if (ox && oy) return ORC_ERR_NESTING;
+    }
+  }
+  return ORC_OK;
+}
+
+orc_state* orc_create(const orc_block* blocks, int nblocks, const double* const* bathy,
+                      const float* const* manning, const orc_params* p, int* err) {
+  int e = ORC_OK;
+  if (!blocks || nblocks <= 0 || !bathy || !manning || !p || !(p->dt > 0) || !(p->g > 0))
+    e = ORC_ERR_INVALID_ARG;
+  for (int k = 0; e == ORC_OK && k < nblocks; ++k)
+    if (!bathy[k] || !manning[k]) e = ORC_ERR_INVALID_ARG;
+  if (e == ORC_OK) e = check_blocks(blocks, nblocks, bathy, p);
+  if (e != ORC_OK) {
+    if (err) *err = e;
+    return NULL;
+  }
+  orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
+  if (!s) goto oom;
+  s->b = (oblk*)calloc((size_t)nblocks, sizeof(oblk));
+  if (!s->b) goto oom;
+  s->nb = nblocks;
+  s->p = *p;
+  for (int k = 0; k < nblocks; ++k) {
+    oblk* b = &s->b[k];
+    b->d = blocks[k];
+    b->nx = blocks[k].nx;
+    b->ny = blocks[k].ny;
+    b->dx = blocks[k].dx;
+    b->dtdx = p->dt / b->dx;
+    size_t nc = (size_t)b->nx * b->ny;
+    size_t nfx = (size_t)(b->nx + 1) * b->ny;
+    size_t nfy = (size_t)b->nx * (b->ny + 1);
+    b->h = (double*)malloc(nc * sizeof(double));
+    b->n = (double*)malloc(nc * sizeof(double));
+    b->eta = (double*)calloc(nc, sizeof(double));
+    b->eta1 = (double*)calloc(nc, sizeof(double));
+    b->M = (double*)calloc(nfx, sizeof(double));
+    b->M1 = (double*)calloc(nfx, sizeof(double));
+    b->N = (double*)calloc(nfy, sizeof(double));
+    b->N1 = (double*)calloc(nfy, sizeof(double));
+    b->emax = (double*)malloc(nc * sizeof(double));
+    b->arr = (long*)malloc(nc * sizeof(long));
+    if (!b->h || !b->n || !b->eta || !b->eta1 || !b->M || !b->M1 || !b->N || !b->N1 ||
+        !b->emax || !b->arr)
+      goto oom;
+    for (size_t c = 0; c < nc; ++c) {
+      b->h[c] = bathy[k][c];
+      b->n[c] = (double)manning[k][c];
+    }
+  }
+  for (int k = 0; k < nblocks; ++k) orc_set_initial_uplift(s, k, NULL);
+  if (err) *err = ORC_OK;
+  return s;
+oom:
+  orc_destroy(s);
+  if (err) *err = ORC_ERR_OOM;
+  return NULL;
+}
+
+/* R9: output update of one cell, after R8 */
+static void track_cell(oblk* b, size_t c, long step, const orc_params* p) {
+  double e = b->eta1[c];
+  if (b->h[c] + e > p->dry_eps && e > b->emax[c]) {
+    if (b->emax[c] < p->arrival_thr && e >= p->arrival_thr) b->arr[c] = step;
+    b->emax[c] = e;
+  }
+}
+
+/* R10 (dz == NULL: sea at rest) */
+int orc_set_initial_uplift(orc_state* s, int k, const double* dz) {
+  if (!s || k < 0 || k >= s->nb) return ORC_ERR_INVALID_ARG;
+  oblk* b = &s->b[k];
+  size_t nc = (size_t)b->nx * b->ny;
+  for (size_t c = 0; c < nc; ++c) {
+    double h = b->h[c];
+    double e;
+    if (h > 0) {
+      e = dz ? dz[c] : 0.0;
+      if (e < -h) e = -h;
+    } else {
+      e = -h;
+    }
+    b->eta[c] = e;
+    b->eta1[c] = e;
+    b->emax[c] = NEVER_WET;
+    b->arr[c] = -1;
+    track_cell(b, c, 0, &s->p);
+  }
+  memset(b->M, 0, (size_t)(b->nx + 1) * b->ny * sizeof(double));
+  memset(b->M1, 0, (size_t)(b->nx + 1) * b->ny * sizeof(double));
+  memset(b->N, 0, (size_t)b->nx * (b->ny + 1) * sizeof(double));
+  memset(b->N1, 0, (size_t)b->nx * (b->ny + 1) * sizeof(double));
+  b->outflow = 0;
+  b->clip = 0;
+  b->ring = 0;
+  s->step = 0;
+  return ORC_OK;
+}
+
+/* ---- R1 + R5: mass (Eq. 1) over one block, with boundary outflow bookkeeping ---- */
+static void mass_block(oblk* b, const orc_params* p) {
+  const double dtdx = b->dtdx, dx2 = b->dx * b->dx, vol = p->dt * b->dx;
+  for (int j = 0; j < b->ny; ++j) {
+    for (int i = 0; i < b->nx; ++i) {
+      double Mw = b->M[FX(b, i, j)], Me = b->M[FX(b, i + 1, j)];
+      double Ns = b->N[FY(b, i, j)], Nn = b->N[FY(b, i, j + 1)];
+      size_t c = C(b, i, j);
+      double e = b->eta[c] - (dtdx * (Me - Mw) + dtdx * (Nn - Ns));
+      if (b->h[c] + e < 0) {
+        b->clip += (-b->h[c] - e) * dx2;
+        e = -b->h[c];
+      }
+      b->eta1[c] = e;
+    }
+  }
+  /* volume that left through the block's own boundary faces this step */
+  for (int j = 0; j < b->ny; ++j) {
+    b->outflow += vol * (-b->M[FX(b, 0, j)]);
+    b->outflow += vol * b->M[FX(b, b->nx, j)];
+  }
+  for (int i = 0; i < b->nx; ++i) {
+    b->outflow += vol * (-b->N[FY(b, i, 0)]);
+    b->outflow += vol * b->N[FY(b, i, b->ny)];
+  }
+}
+
+/* ---- R8: fine->coarse ring (Listing 5) ---- */
+static void ring_child(orc_state* s, int k) {
+  oblk* c = &s->b[k];
+  oblk* P = &s->b[c->d.parent];
+  int a = c->nx / 3, bb = c->ny / 3;
+  double dx2 = P->dx * P->dx;
+  for (int J = 0; J < bb; ++J) {
+    for (int I = 0; I < a; ++I) {
+      if (!(I == 0 || I == a - 1 || J == 0 || J == bb - 1)) continue;
+      double sum = 0.0;
+      int wet = 0;
+      for (int x = 3 * I; x < 3 * I + 3; ++x) {   /* outer: x (the paper's J) */
+        for (int y = 3 * J; y < 3 * J + 3; ++y) { /* inner: y (the paper's I) */
+          size_t q = C(c, x, y);
+          if (c->h[q] + c->eta1[q] > s->p.dry_eps) {
+            sum = sum + c->eta1[q];
+            wet = wet + 1;
+          }
+        }
+      }
+      if (wet == 0) continue; /* dry patch: the parent keeps its own value */
+      size_t pc = C(P, c->d.i0 + I, c->d.j0 + J);
+      double avg = sum * (1.0 / (double)wet); /* all 9 wet: SUMZ * (1.0/9.0) */
+      if (avg < -P->h[pc]) avg = -P->h[pc];
+      P->ring += (avg - P->eta1[pc]) * dx2;
+      P->eta1[pc] = avg;
+    }
+  }
+}
+
+/* ---- R2/R3 helpers. x-faces (f,j) separate cells (f-1,j) and (f,j). ---- */
+static double dep_x(const oblk* b, int f, int j) {
+  size_t L = C(b, f - 1, j), R = C(b, f, j);
+  return 0.5 * (b->h[L] + b->h[R]) + 0.5 * (b->eta1[L] + b->eta1[R]);
+}
+static double dep_y(const oblk* b, int i, int g) {
+  size_t S = C(b, i, g - 1), Nc = C(b, i, g);
+  return 0.5 * (b->h[S] + b->h[Nc]) + 0.5 * (b->eta1[S] + b->eta1[Nc]);
+}
+/* interior x-face usable by advection */
+static int ok_x(const oblk* b, int f, int j, double eps) {
+  return f >= 1 && f <= b->nx - 1 && j >= 0 && j <= b->ny - 1 && dep_x(b, f, j) > eps;
+}
+static int ok_y(const oblk* b, int i, int g, double eps) {
+  return g >= 1 && g <= b->ny - 1 && i >= 0 && i <= b->nx - 1 && dep_y(b, i, g) > eps;
+}
+/* 4-point mean of N around x-face (f,j), pairs taken along x */
+static double nbar_x(const oblk* b, int f, int j) {
+  return 0.25 * ((b->N[FY(b, f - 1, j)] + b->N[FY(b, f, j)]) +
+                 (b->N[FY(b, f - 1, j + 1)] + b->N[FY(b, f, j + 1)]));
+}
+/* 4-point mean of M around y-face (i,g), pairs taken along y */
+static double mbar_y(const oblk* b, int i, int g) {
+  return 0.25 * ((b->M[FX(b, i, g - 1)] + b->M[FX(b, i, g)]) +
+                 (b->M[FX(b, i + 1, g - 1)] + b->M[FX(b, i + 1, g)]));
+}
+
+/* first-order upwind difference of a face flux phi on the sign of the carrier w:
+ * w > 0: phi0 - phim, w < 0: phip - phi0, w == 0: (phip - phim) / 2.
+ * okm/okp say whether the lower/upper neighbour face is usable. */
+static double upwind(double w, double phim, double phi0, double phip, int okm, int okp) {
+  if (w > 0) return okm ? phi0 - phim : 0.0;
+  if (w < 0) return okp ? phip - phi0 : 0.0;
+  return (okm && okp) ? 0.5 * (phip - phim) : 0.0;
+}
+
+/* M^2/D at x-face (f,j) and M*Nbar/D at x-face (f,j) */
+static double qx(const oblk* b, int f, int j) {
+  double m = b->M[FX(b, f, j)];
+  return (m * m) / dep_x(b, f, j);
+}
+static double rx(const oblk* b, int f, int j) {
+  return (b->M[FX(b, f, j)] * nbar_x(b, f, j)) / dep_x(b, f, j);
+}
+static double qy(const oblk* b, int i, int g) {
+  double v = b->N[FY(b, i, g)];
+  return (v * v) / dep_y(b, i, g);
+}
+static double ry(const oblk* b, int i, int g) {
+  return (b->N[FY(b, i, g)] * mbar_y(b, i, g)) / dep_y(b, i, g);
+}
+
+/* common tail of R2/R3: pressure, friction, semi-implicit update */
+static double flux_update(double m, double across, double Df, double grad, double adv, double nf,
+                          double dtdx, const orc_params* p) {
+  double P = p->g * Df * dtdx * grad;
+  double F = 0.5 * p->dt * p->g * nf * nf * sqrt(m * m + across * across) /
+             (Df * Df * cbrt(Df));
+  return ((1.0 - F) * m - adv - P) / (1.0 + F);
+}
+
+/* R4: a face may carry out of its upwind cell at most a quarter of that cell's water
+ * per step (|flux| <= D_src dx / (4 dt)), so four faces cannot drain a cell below dry. */
+static double limit_outflow(double m, double Dlo, double Dhi, double dx, double dt) {
+  double cap = (m > 0 ? Dlo : Dhi) * dx / (4.0 * dt);
+  if (m > cap) return cap;
+  if (m < -cap) return -cap;
+  return m;
+}
+
+/* R2 + R4 at interior x-face (f,j), 1 <= f <= nx-1 */
+static double xmom(const oblk* b, int f, int j, const orc_params* p) {
+  const double eps = p->dry_eps;
+  size_t L = C(b, f - 1, j), R = C(b, f, j);
+  double eL = b->eta1[L], eR = b->eta1[R], hL = b->h[L], hR = b->h[R];
+  int wL = hL + eL > eps, wR = hR + eR > eps;
+  double m = b->M[FX(b, f, j)];
+  double Df, grad, adv;
+  if (wL && wR) {
+    Df = 0.5 * (hL + hR) + 0.5 * (eL + eR);
+    grad = eR - eL;
+    double ax = upwind(m, ok_x(b, f - 1, j, eps) ? qx(b, f - 1, j) : 0.0, qx(b, f, j),
+                       ok_x(b, f + 1, j, eps) ? qx(b, f + 1, j) : 0.0, ok_x(b, f - 1, j, eps),
+                       ok_x(b, f + 1, j, eps));
+    double nb = nbar_x(b, f, j);
+    double ay = upwind(nb, ok_x(b, f, j - 1, eps) ? rx(b, f, j - 1) : 0.0, rx(b, f, j),
+                       ok_x(b, f, j + 1, eps) ? rx(b, f, j + 1) : 0.0, ok_x(b, f, j - 1, eps),
+                       ok_x(b, f, j + 1, eps));
+    adv = b->dtdx * (ax + ay);
+  } else if (wL && !wR && eL > -hR) {
+    Df = eL + hR;
+    grad = -hR - eL;
+    adv = 0.0;
+  } else if (wR && !wL && eR > -hL) {
+    Df = eR + hL;
+    grad = eR + hL;
+    adv = 0.0;
+  } else {
+    return 0.0;
+  }
+  if (!(Df > eps)) return 0.0;
+  double nf = b->n[L] > b->n[R] ? b->n[L] : b->n[R];
+  double m1 = flux_update(m, nbar_x(b, f, j), Df, grad, adv, nf, b->dtdx, p);
+  if (!(wL && wR) && (wL ? m1 < 0.0 : m1 > 0.0)) return 0.0; /* no flow out of a dry cell */
+  return limit_outflow(m1, hL + eL, hR + eR, b->dx, p->dt);
+}
+
+/* R3 + R4 at interior y-face (i,g), 1 <= g <= ny-1: R2 with x and y exchanged */
+static double ymom(const oblk* b, int i, int g, const orc_params* p) {
+  const double eps = p->dry_eps;
+  size_t S = C(b, i, g - 1), Nc = C(b, i, g);
+  double eS = b->eta1[S], eN = b->eta1[Nc], hS = b->h[S], hN = b->h[Nc];
+  int wS = hS + eS > eps, wN = hN + eN > eps;
+  double v = b->N[FY(b, i, g)];
+  double Df, grad, adv;
+  if (wS && wN) {
+    Df = 0.5 * (hS + hN) + 0.5 * (eS + eN);
+    grad = eN - eS;
+    double ay = upwind(v, ok_y(b, i, g - 1, eps) ? qy(b, i, g - 1) : 0.0, qy(b, i, g),
+                       ok_y(b, i, g + 1, eps) ? qy(b, i, g + 1) : 0.0, ok_y(b, i, g - 1, eps),
+                       ok_y(b, i, g + 1, eps));
+    double mb = mbar_y(b, i, g);
+    double ax = upwind(mb, ok_y(b, i - 1, g, eps) ? ry(b, i - 1, g) : 0.0, ry(b, i, g),
+                       ok_y(b, i + 1, g, eps) ? ry(b, i + 1, g) : 0.0, ok_y(b, i - 1, g, eps),
+                       ok_y(b, i + 1, g, eps));
+    adv = b->dtdx * (ay + ax);
+  } else if (wS && !wN && eS > -hN) {
+    Df = eS + hN;
+    grad = -hN - eS;
+    adv = 0.0;
+  } else if (wN && !wS && eN > -hS) {
+    Df = eN + hS;
+    grad = eN + hS;
+    adv = 0.0;
+  } else {
+    return 0.0;
+  }
+  if (!(Df > eps)) return 0.0;
+  double nf = b->n[S] > b->n[Nc] ? b->n[S] : b->n[Nc];
+  double v1 = flux_update(v, mbar_y(b, i, g), Df, grad, adv, nf, b->dtdx, p);
+  if (!(wS && wN) && (wS ? v1 < 0.0 : v1 > 0.0)) return 0.0; /* no flow out of a dry cell */
+  return limit_outflow(v1, hS + eS, hN + eN, b->dx, p->dt);
+}
+
+/* R6: radiation flux leaving through an edge next to cell c (sign: +1 east/north) */
+static double radiate(const oblk* b, size_t c, double sign, const orc_params* p) {
+  double h = b->h[c], e = b->eta1[c];
+  if (!(h + e > p->dry_eps)) return 0.0;
+  return sign * (sqrt(p->g * (h > 0 ? h : 0.0)) * e);
+}
+
+/* ---- R2-R4 + R6: momentum (Eqs. 2-3) over one block ---- */
+static void momentum_block(oblk* b, const orc_params* p) {
+  const int nx = b->nx, ny = b->ny;
+  for (int j = 0; j < ny; ++j)
+    for (int f = 1; f <= nx - 1; ++f) b->M1[FX(b, f, j)] = xmom(b, f, j, p);
+  for (int g = 1; g <= ny - 1; ++g)
+    for (int i = 0; i < nx; ++i) b->N1[FY(b, i, g)] = ymom(b, i, g, p);
+  if (b->d.parent >= 0) { /* child edges are set by R7 after all blocks */
+    for (int j = 0; j < ny; ++j) {
+      b->M1[FX(b, 0, j)] = b->M[FX(b, 0, j)];
+      b->M1[FX(b, nx, j)] = b->M[FX(b, nx, j)];
+    }
+    for (int i = 0; i < nx; ++i) {
+      b->N1[FY(b, i, 0)] = b->N[FY(b, i, 0)];
+      b->N1[FY(b, i, ny)] = b->N[FY(b, i, ny)];
+    }
+    return;
+  }
+  for (int j = 0; j < ny; ++j) {
+    b->M1[FX(b, 0, j)] =
+        b->d.bc[0] == ORC_BC_RADIATION ? radiate(b, C(b, 0, j), -1.0, p) : 0.0;
+    b->M1[FX(b, nx, j)] =
+        b->d.bc[1] == ORC_BC_RADIATION ? radiate(b, C(b, nx - 1, j), 1.0, p) : 0.0;
+  }
+  for (int i = 0; i < nx; ++i) {
+    b->N1[FY(b, i, 0)] =
+        b->d.bc[2] == ORC_BC_RADIATION ? radiate(b, C(b, i, 0), -1.0, p) : 0.0;
+    b->N1[FY(b, i, ny)] =
+        b->d.bc[3] == ORC_BC_RADIATION ? radiate(b, C(b, i, ny - 1), 1.0, p) : 0.0;
+  }
+}
+
+/* ---- R7: coarse->fine edge fluxes ---- */
+/* value for fine face number t along an edge whose coarse faces are v(k), k = 0..K-1 */
+static double interp_edge(const double* v, int K, int t) {
+  int k = t / 3, sub = t % 3;
+  if (sub == 1) return v[k];
+  int kn = sub == 0 ? k - 1 : k + 1;
+  if (kn < 0) kn = 0;
+  if (kn > K - 1) kn = K - 1;
+  return (2.0 * v[k] + v[kn]) / 3.0;
+}
+
+static void edges_child(orc_state* s, int k) {
+  oblk* c = &s->b[k];
+  const oblk* P = &s->b[c->d.parent];
+  int a = c->nx / 3, bb = c->ny / 3, i0 = c->d.i0, j0 = c->d.j0;
+  double* v = (double*)malloc((size_t)(a > bb ? a : bb) * sizeof(double));
+  if (!v) abort();
+  /* west and east: parent x-faces i0 and i0+a, parent rows j0..j0+bb-1 */
+  for (int side = 0; side < 2; ++side) {
+    int F = side == 0 ? i0 : i0 + a, f = side == 0 ? 0 : c->nx;
+    for (int t = 0; t < bb; ++t) v[t] = P->M1[FX(P, F, j0 + t)];
+    for (int j = 0; j < c->ny; ++j) c->M1[FX(c, f, j)] = interp_edge(v, bb, j);
+  }
+  /* south and north: parent y-faces j0 and j0+bb, parent columns i0..i0+a-1 */
+  for (int side = 0; side < 2; ++side) {
+    int G = side == 0 ? j0 : j0 + bb, g = side == 0 ? 0 : c->ny;
+    for (int t = 0; t < a; ++t) v[t] = P->N1[FY(P, i0 + t, G)];
+    for (int i = 0; i < c->nx; ++i) c->N1[FY(c, i, g)] = interp_edge(v, a, i);
+  }
+  free(v);
+}
+
+static void swap_ptr(double** a, double** b) {
+  double* t = *a;
+  *a = *b;
+  *b = t;
+}
+
+int orc_step(orc_state* s, int nsteps) {
+  if (!s || nsteps < 0) return ORC_ERR_INVALID_ARG;
+  for (int it = 0; it < nsteps; ++it) {
+    long step = s->step + 1;
+    for (int k = 0; k < s->nb; ++k) mass_block(&s->b[k], &s->p);
+    for (int k = s->nb - 1; k >= 0; --k) /* finest first */
+      if (s->b[k].d.parent >= 0) ring_child(s, k);
+    for (int k = 0; k < s->nb; ++k) {
+      oblk* b = &s->b[k];
+      for (size_t c = 0; c < (size_t)b->nx * b->ny; ++c) track_cell(b, c, step, &s->p);
+    }
+    for (int k = 0; k < s->nb; ++k) momentum_block(&s->b[k], &s->p);
+    for (int k = 0; k < s->nb; ++k)
+      if (s->b[k].d.parent >= 0) edges_child(s, k);
+    for (int k = 0; k < s->nb; ++k) {
+      oblk* b = &s->b[k];
+      swap_ptr(&b->eta, &b->eta1);
+      swap_ptr(&b->M, &b->M1);
+      swap_ptr(&b->N, &b->N1);
+    }
+    s->step = step;
+  }
+  return ORC_OK;
+}
+
+long orc_steps_done(const orc_state* s) { return s ? s->step : -1; }
+
+int orc_get_state(const orc_state* s, int k, double* eta, double* M, double* N) {
+  if (!s || k < 0 || k >= s->nb) return ORC_ERR_INVALID_ARG;
+  const oblk* b = &s->b[k];
+  if (eta) memcpy(eta, b->eta, (size_t)b->nx * b->ny * sizeof(double));
+  if (M) memcpy(M, b->M, (size_t)(b->nx + 1) * b->ny * sizeof(double));
+  if (N) memcpy(N, b->N, (size_t)b->nx * (b->ny + 1) * sizeof(double));
+  return ORC_OK;
+}
+
+int orc_set_state(orc_state* s, int k, const double* eta, const double* M, const double* N) {
+  if (!s || k < 0 || k >= s->nb) return ORC_ERR_INVALID_ARG;
+  oblk* b = &s->b[k];
+  if (eta) memcpy(b->eta, eta, (size_t)b->nx * b->ny * sizeof(double));
+  if (M) memcpy(b->M, M, (size_t)(b->nx + 1) * b->ny * sizeof(double));
+  if (N) memcpy(b->N, N, (size_t)b->nx * (b->ny + 1) * sizeof(double));
+  return ORC_OK;
+}
+
+int orc_get_max_height(const orc_state* s, int k, double* out) {
+  if (!s || k < 0 || k >= s->nb || !out) return ORC_ERR_INVALID_ARG;
+  const oblk* b = &s->b[k];
+  for (size_t c = 0; c < (size_t)b->nx * b->ny; ++c)
+    out[c] = b->emax[c] == NEVER_WET ? NAN : b->emax[c];
+  return ORC_OK;
+}
+
+int orc_get_max_depth(const orc_state* s, int k, double* out) {
+  if (!s || k < 0 || k >= s->nb || !out) return ORC_ERR_INVALID_ARG;
+  const oblk* b = &s->b[k];
+  for (size_t c = 0; c < (size_t)b->nx * b->ny; ++c)
+    out[c] = b->emax[c] == NEVER_WET ? 0.0 : b->h[c] + b->emax[c];
+  return ORC_OK;
+}
+
+int orc_get_arrival_time(const orc_state* s, int k, double* out) {
+  if (!s || k < 0 || k >= s->nb || !out) return ORC_ERR_INVALID_ARG;
+  const oblk* b = &s->b[k];
+  for (size_t c = 0; c < (size_t)b->nx * b->ny; ++c)
+    out[c] = b->arr[c] < 0 ? -1.0 : (double)b->arr[c] * s->p.dt;
+  return ORC_OK;
+}
+
+int orc_get_budget(const orc_state* s, int k, double* out) {
+  if (!s || k < 0 || k >= s->nb || !out) return ORC_ERR_INVALID_ARG;
+  const oblk* b = &s->b[k];
+  double v = 0.0;
+  for (size_t c = 0; c < (size_t)b->nx * b->ny; ++c) v += b->h[c] + b->eta[c];
+  out[0] = v * (b->dx * b->dx);
+  out[1] = b->outflow;
+  out[2] = b->clip;
+  out[3] = b->ring;
+  return ORC_OK;
+}

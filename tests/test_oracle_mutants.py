@@ -1,0 +1,83 @@
+"""The pins are strong enough: plant one plausible mistake at a time in a copy of
+the oracle's C source (on the CPU), rebuild it, and check that at least one pin of
+test_oracle_pins fails. The product code is never touched."""
+import functools
+import os
+import sys
+import os
+import subprocess
+import types
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+import test_oracle_pins as pins  # noqa: E402
+
+# (name, text in rti_oracle.c, replacement): each one a mistake a port could make
+MUTANTS = [
+    ("mass: flux sum instead of difference", "dtdx * (Me - Mw)", "dtdx * (Me + Mw)"),
+    ("mass: N faces swapped", "dtdx * (Nn - Ns)", "dtdx * (Ns - Nn)"),
+    ("pressure: wrong sign", "grad = eR - eL;", "grad = eL - eR;"),
+    ("pressure: still-water depth only", "Df = 0.5 * (hL + hR) + 0.5 * (eL + eR);",
+     "Df = 0.5 * (hL + hR);"),
+    ("pressure: y uses the x stencil", "grad = eN - eS;", "grad = eN - eN;"),
+    ("friction: n instead of n^2", "p->g * nf * nf *", "p->g * nf *"),
+    ("friction: D^(4/3) instead of D^(7/3)", "(Df * Df * cbrt(Df))", "(Df * cbrt(Df))"),
+    ("advection: downwind on the x term", "if (w > 0) return okm ? phi0 - phim : 0.0;",
+     "if (w > 0) return okp ? phip - phi0 : 0.0;"),
+    ("advection: Nbar from the wrong row",
+     "(b->N[FY(b, f - 1, j + 1)] + b->N[FY(b, f, j + 1)])",
+     "(b->N[FY(b, f - 1, j)] + b->N[FY(b, f, j)])"),
+    ("flood: dry cell's ground sign", "} else if (wL && !wR && eL > -hR) {",
+     "} else if (wL && !wR && eL > hR) {"),
+    ("radiation: inward", "return sign * (sqrt(", "return -sign * (sqrt("),
+    ("nesting: fine faces not interpolated", "return (2.0 * v[k] + v[kn]) / 3.0;",
+     "return v[kn];"),
+    ("nesting: ring mean without the 1/count", "double avg = sum * (1.0 / (double)wet);",
+     "double avg = sum * (1.0 / 8.0);"),
+    ("outputs: strict arrival threshold", "e >= p->arrival_thr", "e > p->arrival_thr"),
+    ("outputs: max tracked on dry cells", "if (b->h[c] + e > p->dry_eps && e > b->emax[c])",
+     "if (e > b->emax[c])"),
+]
+
+# cheapest first; each takes the oracle module as its only argument
+BATTERY = [
+    pins.test_cfl_and_nesting_rejected,
+    pins.test_max_and_arrival_are_functions_of_history,
+    pins.test_nest_constant_field_ring_average,
+    pins.test_nest_edge_flux_reproduces_linear_profile,
+    pins.test_mirror_and_transpose_symmetry_bitwise,
+    pins.test_friction_matches_manning_ode,
+    pins.test_radiation_west_edge_absorbs,
+    functools.partial(pins.test_standing_wave_discrete_period, cfl=0.7),
+    pins.test_budget_closes_with_drying_and_radiation,
+    pins.test_nested_budget_closes,
+    pins.test_nested_plane_wave_matches_fine_grid,
+    pins.test_closed_basin_mass_conservation,
+    pins.test_lake_at_rest_nested_bitwise,
+    pins.test_thacker_parabolic_bowl,
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(oracle_mod, tmp_path, name, old, new):
+    src = open(oracle_mod.SRC).read()
+    assert src.count(old) >= 1, f"mutation site missing: {old}"
+    csrc = tmp_path / "rti_oracle.c"
+    csrc.write_text(src.replace(old, new))
+    hdr = os.path.join(os.path.dirname(oracle_mod.SRC), "rti_oracle.h")
+    (tmp_path / "rti_oracle.h").write_text(open(hdr).read())
+    so = str(tmp_path / "mut.so")
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", so, str(csrc), "-lm"])
+    fake = types.SimpleNamespace(
+        Oracle=functools.partial(oracle_mod.Oracle, lib_path=so),
+        OracleError=oracle_mod.OracleError,
+        from_scenario=functools.partial(oracle_mod.from_scenario, lib_path=so),
+        SRC=oracle_mod.SRC)
+    for pin in BATTERY:
+        try:
+            pin(fake)
+        except (AssertionError, oracle_mod.OracleError, FloatingPointError, ValueError):
+            return  # caught
+    pytest.fail(f"no pin caught the planted mistake: {name}")

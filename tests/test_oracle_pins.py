@@ -1,0 +1,416 @@
+"""Pins of the FP64 oracle against what the mathematics fixes (no GPU).
+
+Each test checks the oracle against something other than itself: an exact
+invariant of the discrete scheme (mass conservation, the volume budget, lake at
+rest, mirror symmetry), a closed-form solution of the PDEs (Thacker's bowl, the
+friction ODE, the linear standing wave and its discrete dispersion relation) or
+a physical bound (radiation reflection, nested vs fine-grid solution).
+"""
+import math
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+import numpy as np
+import pytest
+
+G = 9.81
+
+
+def single(nx, ny, dx, h, n=0.0, bc=(0, 0, 0, 0)):
+    blk = dict(level=1, parent=-1, nx=nx, ny=ny, i0=0, j0=0, dx=dx, bc=bc)
+    hh = np.broadcast_to(np.asarray(h, np.float64), (ny, nx)).copy()
+    nn = np.broadcast_to(np.asarray(n, np.float32), (ny, nx)).copy()
+    return blk, hh, nn
+
+
+def centres(n, dx):
+    return (np.arange(n) + 0.5) * dx
+
+
+# ----------------------------------------------------------------------------- Eq. 1
+def test_closed_basin_mass_conservation(oracle_mod):
+    """Walls, no drying: the flux differences of Eq. 1 telescope, so sum(eta) is
+    constant to rounding over 10^4 steps (with friction and advection on)."""
+    nx, ny, dx = 64, 48, 2000.0
+    x, y = centres(nx, dx), centres(ny, dx)
+    h = 200.0 + 100.0 * np.sin(x[None, :] / 9e3) * np.cos(y[:, None] / 7e3)
+    blk, hh, nn = single(nx, ny, dx, h, n=0.025)
+    o = oracle_mod.Oracle([blk], [hh], [nn], dt=10.0)
+    dz = 3.0 * np.exp(-((x[None, :] - 40e3) ** 2 + (y[:, None] - 50e3) ** 2) / (2 * 8e3**2))
+    o.set_initial_uplift(0, dz)
+    e0, _, _ = o.get_state(0)
+    s0, a0 = e0.sum(), np.abs(e0).sum()
+    v0 = o.budget(0)["volume"]
+    o.step(10000)
+    e1, _, _ = o.get_state(0)
+    b = o.budget(0)
+    assert np.abs(e1).max() > 1e-3  # the wave is still there
+    assert abs(e1.sum() - s0) <= 1e-12 * a0
+    assert abs(b["volume"] - v0) <= 1e-13 * v0
+    assert b["outflow"] == 0.0 and b["clip"] == 0.0 and b["ring"] == 0.0
+
+
+def test_budget_closes_with_drying_and_radiation(oracle_mod):
+    """Beach that dries and floods plus an open west edge: V(t) = V0 - outflow + clip."""
+    nx, ny, dx = 80, 40, 500.0
+    x = centres(nx, dx)
+    prof = np.where(x < 25e3, 60.0, 60.0 - (x - 25e3) * 0.006)  # beach rising to land
+    h = np.tile(prof, (ny, 1))
+    blk, hh, nn = single(nx, ny, dx, h, n=0.03, bc=(1, 0, 0, 0))
+    o = oracle_mod.Oracle([blk], [hh], [nn], dt=2.0)
+    y = centres(ny, dx)
+    o.set_initial_uplift(0, 4.0 * np.exp(-((x[None, :] - 20e3) ** 2) / (2 * 3e3**2)) +
+                         0 * y[:, None])
+    v0 = o.budget(0)["volume"]
+    wet0 = hh + o.get_state(0)[0] > 1e-3
+    flooded = np.zeros_like(wet0)
+    for _ in range(30):
+        o.step(100)
+        flooded |= (hh + o.get_state(0)[0] > 1e-3) & ~wet0
+    b = o.budget(0)
+    assert b["outflow"] != 0 and flooded.sum() > 40  # the shore moved
+    assert abs(b["volume"] - (v0 - b["outflow"] + b["clip"])) <= 1e-12 * v0
+
+
+# ----------------------------------------------------------------------- Eqs. 2-3 at rest
+def _rest_hierarchy(scen):
+    sc = scen.coastal_hierarchy("rest", 11, (60, 54, 810.0), [(1, 36, 36), (1, 27, 27)],
+                                dt=0.5, steps=0, shelf_w=8e3, slope_w=10e3, wiggle=1e3,
+                                coast_frac=0.6, land_frac=0.4, relief_amp=3.0)
+    return sc
+
+
+def test_lake_at_rest_nested_bitwise(oracle_mod):
+    """eta = 0 on sea, -h on land, no flux, over rough bathymetry with land and three
+    nested levels: every term of Eqs. 2-3 vanishes, bitwise, for 10^4 steps."""
+    from paper_2408_07609_gb300 import scenarios as S
+
+    sc = _rest_hierarchy(S)
+    assert any((h <= 0).any() for h in sc.bathy) and any((h > 0).any() for h in sc.bathy)
+    o = oracle_mod.Oracle(sc.blocks, sc.bathy, sc.manning, sc.dt)
+    o.step(10000)
+    for k in range(len(sc.blocks)):
+        e, M, N = o.get_state(k)
+        rest = np.where(sc.bathy[k] > 0, 0.0, -sc.bathy[k])
+        assert np.array_equal(e, rest)
+        assert not M.any() and not N.any()
+        b = o.budget(k)
+        assert b["clip"] == 0 and b["outflow"] == 0 and b["ring"] == 0
+
+
+# ------------------------------------------------------------------ linear standing wave
+@pytest.mark.parametrize("cfl", [0.3, 0.7])
+def test_standing_wave_discrete_period(oracle_mod, cfl):
+    """Flat closed basin, mode cos(pi x / L), amplitude 1e-6 h, no friction. The linear
+    leap-frog staggered scheme has the exact discrete dispersion relation
+    sin(w dt / 2) = (c dt / dx) sin(k dx / 2); the measured period must match it to
+    1e-5 (and differs visibly from the continuum 2L/c at coarse resolution)."""
+    nx, ny, dx, h = 24, 4, 1000.0, 100.0
+    c = math.sqrt(G * h)
+    dt = cfl * dx / c
+    blk, hh, nn = single(nx, ny, dx, h)
+    o = oracle_mod.Oracle([blk], [hh], [nn], dt=dt)
+    L = nx * dx
+    k = math.pi / L
+    x = centres(nx, dx)
+    a = 1e-6 * h
+    o.set_initial_uplift(0, np.tile(a * np.cos(k * x), (ny, 1)))
+    w = 2.0 / dt * math.asin(c * dt / dx * math.sin(k * dx / 2))
+    T_disc, T_cont = 2 * math.pi / w, 2 * L / c
+    nsteps = int(2.5 * T_disc / dt)
+    series = []
+    for _ in range(nsteps):
+        o.step(1)
+        series.append(o.get_state(0)[0][1, 0])
+    s = np.array(series)
+    # cos(w dt) from the two-step recurrence where |eta| is not small
+    mid = s[1:-1]
+    sel = np.abs(mid) > 0.5 * a
+    cos_wdt = np.median((s[2:][sel] + s[:-2][sel]) / (2 * mid[sel]))
+    T_fit = 2 * math.pi * dt / math.acos(cos_wdt)
+    assert abs(T_fit - T_disc) <= 1e-5 * T_disc
+    assert abs(T_disc - T_cont) > 1e-5 * T_cont  # the discrete period is what is pinned
+    # amplitude neither grows nor decays (neutral leap-frog)
+    assert abs(np.abs(s).max() - a) < 0.02 * a
+
+
+# ---------------------------------------------------------------- Thacker parabolic bowl
+def thacker(r, t, h0, a, r0):
+    A = (a**4 - r0**4) / (a**4 + r0**4)
+    w = math.sqrt(8 * G * h0) / a
+    cw = math.cos(w * t)
+    return h0 * (math.sqrt(1 - A * A) / (1 - A * cw) - 1 -
+                 (r * r / (a * a)) * ((1 - A * A) / (1 - A * cw) ** 2 - 1)), w
+
+
+def run_thacker(oracle_mod, dx, h0=50.0, a=80e3, r0=70e3, dt=5.0):
+    half = 100e3  # the shoreline swings between r0 = 70 km and 91.4 km
+    n = int(round(2 * half / dx))
+    x = centres(n, dx) - half
+    r = np.sqrt(x[None, :] ** 2 + x[:, None] ** 2)
+    h = h0 * (1 - r**2 / a**2)
+    blk, hh, nn = single(n, n, dx, h)
+    o = oracle_mod.Oracle([blk], [hh], [nn], dt=dt)
+    eta0, w = thacker(r, 0.0, h0, a, r0)
+    o.set_initial_uplift(0, eta0)
+    T = 2 * math.pi / w
+    errs = []
+    done = 0
+    for frac in (0.5, 1.0):
+        target = int(round(frac * T / dt))
+        o.step(target - done)
+        done = target
+        ex, _ = thacker(r, done * dt, h0, a, r0)
+        e, _, _ = o.get_state(0)
+        both = (h + ex > 0) & (h + e > 1e-3)
+        errs.append(np.abs(e - ex)[both].mean() / h0)
+    assert o.budget(0)["clip"] == 0.0  # the outflow limit keeps every cell non-negative
+    return errs
+
+
+def test_thacker_parabolic_bowl(oracle_mod):
+    """Thacker (1981) analytic moving-shoreline solution of the nonlinear SWE (Eqs. 1-3
+    with n = 0) tests advection, the wet/dry front and the depth terms together.
+    A = (a^4 - r0^4)/(a^4 + r0^4) = 0.26: the shoreline moves 21 km each half period."""
+    e1 = run_thacker(oracle_mod, 1000.0)
+    e2 = run_thacker(oracle_mod, 500.0)
+    for e in e1 + e2:
+        assert e <= 0.03
+    # refinement lowers the error
+    assert e2[0] < 0.8 * e1[0] and e2[1] < 0.8 * e1[1]
+
+
+# -------------------------------------------------------------------- mirror symmetry
+def test_mirror_and_transpose_symmetry_bitwise(oracle_mod):
+    """Symmetric square basin with a symmetric island (drying on), centred source:
+    x-mirror, y-mirror and transposition are exact symmetries of Eqs. 1-3 and of the
+    scheme's operation order, so they hold bitwise."""
+    n, dx = 60, 1000.0
+    x = centres(n, dx) - n * dx / 2
+    r = np.sqrt(x[None, :] ** 2 + x[:, None] ** 2)
+    h = 80.0 - 95.0 * np.exp(-(r / 6e3) ** 2)  # island in the middle
+    blk, hh, nn = single(n, n, dx, h, n=0.03)
+    o = oracle_mod.Oracle([blk], [hh], [nn], dt=5.0)
+    ring = 2.5 * np.exp(-((r - 15e3) / 4e3) ** 2)
+    o.set_initial_uplift(0, ring)
+    wet0 = hh + o.get_state(0)[0] > 1e-3
+    flips = 0
+    for _ in range(4):
+        o.step(150)
+        e, M, N = o.get_state(0)
+        assert np.array_equal(e, e[:, ::-1])
+        assert np.array_equal(e, e[::-1, :])
+        assert np.array_equal(e, e.T)
+        assert np.array_equal(M, -M[:, ::-1])
+        assert np.array_equal(N, -N[::-1, :])
+        assert np.array_equal(M, N.T)
+        flips += ((hh + e > 1e-3) != wet0).sum()
+    assert flips > 0  # the island's shore flooded and dried
+
+
+# ------------------------------------------------------------------------- friction
+def test_friction_matches_manning_ode(oracle_mod):
+    """Uniform flux over a flat bed, far from the walls: Eq. 2 reduces to
+    dM/dt = -g n^2 M|M| / h^(7/3), solved by M0 / (1 + k M0 t). The semi-implicit
+    scheme is first order in time: the error halves with dt."""
+    nx, ny, dx, h, nman, M0 = 200, 20, 500.0, 5.0, 0.03, 2.0
+    k = G * nman**2 / h ** (7.0 / 3.0)
+    errs = []
+    for dt in (4.0, 2.0):
+        blk, hh, nn = single(nx, ny, dx, h, n=nman)
+        o = oracle_mod.Oracle([blk], [hh], [nn], dt=dt)
+        M = np.full((ny, nx + 1), M0)
+        M[:, 0] = M[:, -1] = 0.0
+        o.set_state(0, eta=np.zeros((ny, nx)), M=M, N=np.zeros((ny + 1, nx)))
+        steps = int(round(40.0 / dt))
+        o.step(steps)
+        _, M1, _ = o.get_state(0)
+        exact = M0 / (1 + k * M0 * steps * dt)
+        mid = M1[:, nx // 2 - 5: nx // 2 + 5]
+        assert np.all(mid == mid[0, 0])  # untouched by the walls
+        errs.append(abs(mid[0, 0] - exact) / exact)
+    assert errs[0] < 2e-3
+    assert 1.6 < errs[0] / errs[1] < 2.4
+
+
+# ------------------------------------------------------------------------- radiation
+def test_radiation_west_edge_absorbs(oracle_mod):
+    """A left-going linear long wave (M = -c eta) leaves through the radiation edge;
+    the energy left in the channel afterwards is < 2 % of the initial energy."""
+    nx, ny, dx, h = 400, 4, 1000.0, 100.0
+    c = math.sqrt(G * h)
+    dt = 10.0
+    blk, hh, nn = single(nx, ny, dx, h, bc=(1, 0, 0, 0))
+    o = oracle_mod.Oracle([blk], [hh], [nn], dt=dt)
+    x = centres(nx, dx)
+    xf = np.arange(nx + 1) * dx
+    amp = 0.05
+    eta = np.tile(amp * np.exp(-((x - 200e3) / 15e3) ** 2), (ny, 1))
+    M = np.tile(-c * amp * np.exp(-((xf - 200e3) / 15e3) ** 2), (ny, 1))
+    M[:, -1] = 0.0
+    o.set_state(0, eta=eta, M=M, N=np.zeros((ny + 1, nx)))
+
+    def energy():
+        e, M, N = o.get_state(0)
+        return 0.5 * G * (e**2).sum() + 0.5 * ((M**2).sum() + (N**2).sum()) / h
+
+    E0 = energy()
+    o.step(int(round(320e3 / c / dt)))
+    assert energy() < 0.02 * E0
+
+
+# ------------------------------------------------------------------------- nesting
+def nested_flat(dxp=300.0, h=50.0, npx=90, npy=30, cx=30, cw=30, cy=6, ch=18, bc=(1, 1, 0, 0)):
+    blocks = [dict(level=1, parent=-1, nx=npx, ny=npy, i0=0, j0=0, dx=dxp, bc=bc),
+              dict(level=2, parent=0, nx=3 * cw, ny=3 * ch, i0=cx, j0=cy, dx=dxp / 3, bc=(0,) * 4)]
+    bathy = [np.full((npy, npx), h), np.full((3 * ch, 3 * cw), h)]
+    man = [np.zeros((npy, npx), np.float32), np.zeros((3 * ch, 3 * cw), np.float32)]
+    return blocks, bathy, man
+
+
+def test_nest_constant_field_ring_average(oracle_mod):
+    """A constant child field averages (Listing 5: sum of 9 times 1/9) to itself within
+    one ulp on the parent's ring cells, and inner parent cells keep their own value."""
+    blocks, bathy, man = nested_flat()
+    o = oracle_mod.Oracle(blocks, bathy, man, dt=2.0)
+    cval = 0.123456789
+    o.set_state(1, eta=np.full((54, 90), cval))
+    o.step(1)
+    e, _, _ = o.get_state(0)
+    I0, J0, a, b = 30, 6, 30, 18
+    ring = np.zeros_like(e, bool)
+    ring[J0:J0 + b, I0:I0 + a] = True
+    ring[J0 + 1:J0 + b - 1, I0 + 1:I0 + a - 1] = False
+    assert np.all(np.abs(e[ring] - cval) <= np.spacing(cval))
+    assert np.all(e[J0 + 1:J0 + b - 1, I0 + 1:I0 + a - 1] == 0.0)
+    assert o.budget(0)["ring"] > 0
+
+
+def test_nest_edge_flux_reproduces_linear_profile(oracle_mod):
+    """Steady shear flow M(y) = a + b y over a flat bed (no friction, N = 0): the parent
+    keeps it exactly, and linear interpolation along a child edge must reproduce the
+    straight line at every fine face centre away from the clamped segment ends."""
+    blocks, bathy, man = nested_flat(bc=(0, 0, 0, 0))
+    o = oracle_mod.Oracle(blocks, bathy, man, dt=2.0)
+    dxp = blocks[0]["dx"]
+    yp = centres(30, dxp)
+    Mp = np.tile((0.3 + 2e-5 * yp)[:, None], (1, 91))
+    Mp[:, 0] = Mp[:, -1] = 0.0
+    o.set_state(0, M=Mp)
+    o.step(1)
+    _, Mc, _ = o.get_state(1)
+    J0 = blocks[1]["j0"]
+    yc = J0 * dxp + centres(54, dxp / 3)
+    want = 0.3 + 2e-5 * yc
+    for f in (0, 90):  # west and east edges
+        got = Mc[3:-3, f]
+        assert np.allclose(got, want[3:-3], rtol=1e-14, atol=0)
+        assert not np.allclose(Mc[3:-3, f], np.repeat(Mp[J0 + 1:J0 + 17, 31], 3), rtol=1e-9)
+
+
+def test_nested_budget_closes(oracle_mod):
+    """With nesting, each block's budget closes: V = V0 - outflow + clip + ring."""
+    from paper_2408_07609_gb300 import scenarios as S
+
+    sc = S.coastal_hierarchy("b", 5, (60, 54, 810.0), [(1, 36, 36), (1, 27, 27)], dt=0.5,
+                             steps=0, shelf_w=8e3, slope_w=10e3, wiggle=1e3, coast_frac=0.6,
+                             land_frac=0.4, source=dict(kind="gauss", sigma=4e3, peak=2.0))
+    o = oracle_mod.Oracle(sc.blocks, sc.bathy, sc.manning, sc.dt)
+    for k, dz in enumerate(sc.uplift):
+        if dz is not None:
+            o.set_initial_uplift(k, dz)
+    v0 = [o.budget(k)["volume"] for k in range(3)]
+    o.step(2000)
+    for k in range(3):
+        b = o.budget(k)
+        assert abs(b["volume"] - (v0[k] - b["outflow"] + b["clip"] + b["ring"])) <= 1e-12 * v0[k]
+    assert o.budget(1)["outflow"] != 0 and o.budget(0)["ring"] != 0
+
+
+def test_nested_plane_wave_matches_fine_grid(oracle_mod):
+    """A long plane wave crossing a flat nested patch: inside the patch the nested
+    solution (coarse flux interpolated in, 3x3 mean fed back) stays within 2 % of the
+    amplitude of a single grid at the child's resolution everywhere."""
+    dxp, h, amp = 300.0, 50.0, 0.05
+    npx, npy = 150, 30
+    blocks, bathy, man = nested_flat(dxp, h, npx=npx, npy=npy, cx=60, cw=30, cy=6, ch=18,
+                                     bc=(1, 1, 0, 0))
+    dt = 2.0
+    c = math.sqrt(G * h)
+    lam = 12e3
+    x0 = 9e3
+
+    def wave(x):
+        return amp * np.exp(-((x - x0) / (lam / 4)) ** 2)
+
+    o = oracle_mod.Oracle(blocks, bathy, man, dt=dt)
+    xp = centres(npx, dxp)
+    xfp = np.arange(npx + 1) * dxp
+    o.set_state(0, eta=np.tile(wave(xp), (npy, 1)), M=np.tile(c * wave(xfp), (npy, 1)))
+    xc = 60 * dxp + centres(90, dxp / 3)
+    xfc = 60 * dxp + np.arange(91) * dxp / 3
+    o.set_state(1, eta=np.tile(wave(xc), (54, 1)), M=np.tile(c * wave(xfc), (54, 1)))
+    blk, hh, nn = single(3 * npx, 3 * npy, dxp / 3, h, bc=(1, 1, 0, 0))
+    f = oracle_mod.Oracle([blk], [hh], [nn], dt=dt)
+    xf = centres(3 * npx, dxp / 3)
+    xff = np.arange(3 * npx + 1) * dxp / 3
+    f.set_state(0, eta=np.tile(wave(xf), (3 * npy, 1)), M=np.tile(c * wave(xff), (3 * npy, 1)))
+    worst = 0.0
+    for _ in range(10):
+        o.step(100)
+        f.step(100)
+        ec = o.get_state(1)[0]
+        ef = f.get_state(0)[0][18:18 + 54, 180:180 + 90]
+        worst = max(worst, np.abs(ec - ef).max())
+    assert worst <= 0.02 * amp
+
+
+# ------------------------------------------------------------------------- outputs (R9)
+def test_max_and_arrival_are_functions_of_history(oracle_mod):
+    from paper_2408_07609_gb300 import scenarios as S
+
+    sc = S.config1(nx=48, ny=40)
+    sc.uplift[0][5, 7] = sc.arrival_thr  # a cell exactly at the threshold arrives at t = 0
+    o = oracle_mod.from_scenario(sc)
+    h = sc.bathy[0]
+    e0 = o.get_state(0)[0]
+    hist = [e0]
+    for _ in range(120):
+        o.step(1)
+        hist.append(o.get_state(0)[0])
+    H = np.array(hist)
+    wet = (h[None] + H) > sc.dry_eps
+    masked = np.where(wet, H, -np.inf)
+    emax = masked.max(axis=0)
+    never = ~wet.any(axis=0)
+    got = o.max_height(0)
+    assert np.array_equal(np.isnan(got), never)
+    assert np.array_equal(got[~never], emax[~never])
+    md = o.max_depth(0)
+    assert np.array_equal(md[~never], h[~never] + emax[~never]) and np.all(md[never] == 0)
+    run = np.maximum.accumulate(masked, axis=0)
+    reached = run >= sc.arrival_thr
+    first = np.where(reached.any(axis=0), reached.argmax(axis=0), -1)
+    exp_t = np.where(first >= 0, first * sc.dt, -1.0)
+    assert np.array_equal(o.arrival_time(0), exp_t)
+    assert (first > 0).sum() > 100 and exp_t[5, 7] == 0.0
+
+
+# ------------------------------------------------------------------------- validation
+def test_cfl_and_nesting_rejected(oracle_mod):
+    blk, hh, nn = single(30, 30, 100.0, 1000.0)
+    with pytest.raises(oracle_mod.OracleError) as ei:
+        oracle_mod.Oracle([blk], [hh], [nn], dt=1.0)  # 100 m/s < sqrt(2 g 1000) = 140
+    assert ei.value.code == -2
+    oracle_mod.Oracle([blk], [hh], [nn], dt=0.7)
+    blocks, bathy, man = nested_flat()
+    bad = [dict(b) for b in blocks]
+    bad[1]["i0"] = 2  # closer than 3 parent cells to the edge
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.Oracle(bad, bathy, man, dt=2.0)
+    bad = [dict(b) for b in blocks]
+    bad[1]["dx"] = 99.0
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.Oracle(bad, bathy, man, dt=2.0)
