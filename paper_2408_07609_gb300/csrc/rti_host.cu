@@ -1,0 +1,1054 @@
+// rti_host.cu -- the C ABI (include/rti.h): hierarchy validation, the device arena of a
+// handle, the tile work list of a group of handles, chunk launches and CUDA graphs,
+// batches, and host<->device transfers. No arithmetic of the time step runs here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rti.h"
+#include "rti_launch.h"
+#include "rti_layout.h"
+
+using namespace rti;
+
+namespace rti {
+__global__ void k_advance(ScenDev* sc, const int* nscen, int nsteps);
+__global__ void k_set_scen(ScenDev* sc, int idx, long long base, long long remaining);
+#ifdef RTI_CHECKED
+cudaError_t debug_check_fp32(int* out8);
+cudaError_t debug_check_fp64(int* out8);
+#endif
+}  // namespace rti
+
+namespace {
+
+constexpr int kDefaultTx = 64, kDefaultTy = 16;
+constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at the maximum SM clock
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct BlkMem {
+  size_t eta[2], M[2], N[2], h, emax, man, arr, budget;
+  int pitch;
+  long long rows;
+  int tiles_x, tiles_y;
+};
+
+size_t esize(int prec) { return prec == RTI_FP32 ? 4 : 8; }
+
+// Layout of one handle's arena; returns the total size.
+size_t plan_layout(const rti_block* b, int nb, int prec, int tx, int ty, std::vector<BlkMem>* mem,
+                   size_t* off_status) {
+  size_t off = 0;
+  const size_t es = esize(prec);
+  if (mem) mem->resize(nb);
+  for (int k = 0; k < nb; ++k) {
+    BlkMem m;
+    m.pitch = pitch_for(b[k].nx);
+    m.rows = rows_for(b[k].ny);
+    const size_t plane = (size_t)m.pitch * (size_t)m.rows;
+    auto take = [&](size_t bytes) {
+      size_t o = off;
+      off = align256(off + bytes);
+      return o;
+    };
+    for (int s = 0; s < 2; ++s) m.eta[s] = take(plane * es);
+    for (int s = 0; s < 2; ++s) m.M[s] = take(plane * es);
+    for (int s = 0; s < 2; ++s) m.N[s] = take(plane * es);
+    m.h = take(plane * es);
+    m.emax = take(plane * es);
+    m.man = take(plane * 4);
+    m.arr = take(plane * 4);
+    m.tiles_x = (b[k].nx + tx - 1) / tx;
+    m.tiles_y = (b[k].ny + ty - 1) / ty;
+    m.budget = take((size_t)m.tiles_x * m.tiles_y * 4 * sizeof(double));
+    if (mem) (*mem)[k] = m;
+  }
+  size_t st = off;
+  off = align256(off + 64);
+  if (off_status) *off_status = st;
+  return off;
+}
+
+int validate(const rti_block* bl, int nb, const rti_params* p, std::string* why) {
+  if (!bl || nb <= 0 || !p) {
+    *why = "null descriptor or no blocks";
+    return RTI_ERR_INVALID_ARG;
+  }
+  if (!(p->dt > 0) || !(p->g > 0) || !(p->dry_eps >= 0) ||
+      (p->precision != RTI_FP32 && p->precision != RTI_FP64) ||
+      (p->schedule != RTI_SCHED_PERSISTENT && p->schedule != RTI_SCHED_PER_PASS) ||
+      p->tile_x < 0 || p->tile_y < 0 || p->tile_x % 32 || p->tile_y % 8) {
+    *why = "bad params (dt, g, dry_eps, precision, schedule or tile shape)";
+    return RTI_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < nb; ++k) {
+    const rti_block* d = &bl[k];
+    if (d->nx < 3 || d->ny < 3 || !(d->dx > 0) || d->nx > (1 << 20) || d->ny > (1 << 20)) {
+      *why = "block " + std::to_string(k) + ": bad size or dx";
+      return RTI_ERR_INVALID_ARG;
+    }
+    if (d->parent < 0) {
+      if (d->level != 1) {
+        *why = "block " + std::to_string(k) + ": a root must have level 1";
+        return RTI_ERR_NESTING;
+      }
+      for (int s = 0; s < 4; ++s)
+        if (d->bc[s] != RTI_BC_WALL && d->bc[s] != RTI_BC_RADIATION) {
+          *why = "block " + std::to_string(k) + ": bad boundary kind";
+          return RTI_ERR_INVALID_ARG;
+        }
+      continue;
+    }
+    auto bad = [&](const char* m) {
+      *why = "block " + std::to_string(k) + ": " + m;
+      return RTI_ERR_NESTING;
+    };
+    if (d->parent >= k) return bad("parents must be listed before their children");
+    const rti_block* P = &bl[d->parent];
+    if (d->level != P->level + 1) return bad("level must be parent level + 1");
+    if (d->nx % 3 || d->ny % 3) return bad("child size must be a multiple of 3");
+    if (std::fabs(d->dx * 3.0 - P->dx) > 1e-9 * P->dx) return bad("child dx must be parent dx / 3");
+    if (d->i0 < 3 || d->j0 < 3 || d->i0 + d->nx / 3 > P->nx - 3 || d->j0 + d->ny / 3 > P->ny - 3)
+      return bad("child must lie inside its parent with a 3-cell margin");
+    for (int q = 0; q < k; ++q) {
+      const rti_block* o = &bl[q];
+      if (o->parent != d->parent) continue;
+      bool ox = d->i0 < o->i0 + o->nx / 3 && o->i0 < d->i0 + d->nx / 3;
+      bool oy = d->j0 < o->j0 + o->ny / 3 && o->j0 < d->j0 + d->ny / 3;
+      if (ox && oy) return bad("overlaps a sibling");
+    }
+  }
+  return RTI_OK;
+}
+
+const char* cuda_name(cudaError_t e) { return cudaGetErrorString(e); }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ groups
+struct Group {
+  int prec = RTI_FP64, sched = RTI_SCHED_PERSISTENT, tx = kDefaultTx, ty = kDefaultTy;
+  int chunk = 1;
+  std::vector<rti_handle*> members;
+  std::vector<long long> remaining;  // host mirror of ScenDev.remaining (as enqueued)
+  // device tables
+  char* d_blk = nullptr;
+  size_t cap_blk = 0;  // bytes
+  int* d_kids = nullptr;
+  size_t cap_kids = 0;
+  Tile* d_tiles = nullptr;
+  size_t cap_tiles = 0;
+  int* d_counts = nullptr;  // [0] = ntiles, [1] = nscen
+  ScenDev* d_scen = nullptr;
+  size_t cap_scen = 0;
+  int* d_status = nullptr;
+  Bar* d_bar = nullptr;
+  int grid = 0;
+  long long spin_cycles = kSpinCycles;
+  // pinned staging for table uploads
+  char* h_stage = nullptr;
+  size_t cap_stage = 0;
+  cudaEvent_t staged = nullptr;
+  // graph of one chunk
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_tried = false;
+  cudaStream_t cap_stream = nullptr;
+  int ntiles = 0, nblk = 0, nkids = 0;
+  long long cells = 0;
+  bool dirty = true;
+};
+
+struct rti_handle {
+  int prec = RTI_FP64;
+  rti_params params{};
+  std::vector<rti_block> blocks;
+  std::vector<BlkMem> mem;
+  std::vector<double> sum_h;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  bool own = false;
+  size_t off_status = 0;
+  long long base = 0;  // steps completed including enqueued work
+  std::string err;
+  rti_batch* batch = nullptr;
+  Group* self = nullptr;
+  cudaEvent_t done = nullptr;
+  long long cells = 0;
+  long long h2d = 0, d2h = 0;  // bytes moved by this handle's calls
+};
+
+struct rti_batch {
+  Group g;
+  std::string err;
+  cudaEvent_t done = nullptr;
+};
+
+namespace {
+
+int set_err(std::string* dst, int code, const std::string& msg) {
+  if (dst) *dst = msg;
+  return code;
+}
+
+int cuda_err(std::string* dst, cudaError_t e, const char* what) {
+  if (dst) *dst = std::string(what) + ": " + cuda_name(e);
+  return RTI_ERR_CUDA;
+}
+
+template <class T>
+Blk<T> make_blk(rti_handle* h, int k, int base_index, int scen, int child_first, int child_count,
+                int tx) {
+  const rti_block& d = h->blocks[k];
+  const BlkMem& m = h->mem[k];
+  const rti_params& p = h->params;
+  Blk<T> b;
+  std::memset(&b, 0, sizeof(b));
+  char* A = h->arena;
+  for (int s = 0; s < 2; ++s) {
+    b.eta[s] = (T*)(A + m.eta[s]);
+    b.M[s] = (T*)(A + m.M[s]);
+    b.N[s] = (T*)(A + m.N[s]);
+  }
+  b.h = (const T*)(A + m.h);
+  b.man = (const float*)(A + m.man);
+  b.emax = (T*)(A + m.emax);
+  b.arr = (int*)(A + m.arr);
+  b.nx = d.nx;
+  b.ny = d.ny;
+  b.pitch = m.pitch;
+  b.parent = d.parent < 0 ? -1 : base_index + d.parent;
+  b.i0 = d.i0;
+  b.j0 = d.j0;
+  b.child_first = child_first;
+  b.child_count = child_count;
+  for (int s = 0; s < 4; ++s) b.bc[s] = d.bc[s];
+  b.scen = scen;
+  b.is_child = d.parent >= 0;
+  b.tiles_x = (d.nx + tx - 1) / tx;
+  b.budget = (double*)(A + m.budget);
+  b.status = (int*)(A + h->off_status);
+  const double dt = p.dt, dx = d.dx;
+  b.dtdx = (T)(dt / dx);
+  b.dt = (T)dt;
+  b.g = (T)p.g;
+  b.cfric = (T)(0.5 * dt * p.g);
+  b.eps = (T)p.dry_eps;
+  b.thr = (T)p.arrival_thr;
+  b.dx = (T)dx;
+  b.q4dt = (T)(4.0 * dt);
+  b.dx2 = dx * dx;
+  b.vol = dt * dx;
+  b.eps_d = p.dry_eps;
+#ifdef RTI_CHECKED
+  b.lo = h->arena;
+  b.hi = h->arena + h->arena_bytes;
+#endif
+  return b;
+}
+
+void free_group_dev(Group* g) {
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  g->gexec = nullptr;
+  g->graph_tried = false;
+  cudaFree(g->d_blk);
+  cudaFree(g->d_kids);
+  cudaFree(g->d_tiles);
+  cudaFree(g->d_counts);
+  cudaFree(g->d_scen);
+  cudaFree(g->d_status);
+  cudaFree(g->d_bar);
+  if (g->h_stage) cudaFreeHost(g->h_stage);
+  if (g->staged) cudaEventDestroy(g->staged);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  g->d_blk = nullptr;
+  g->d_kids = nullptr;
+  g->d_tiles = nullptr;
+  g->d_counts = nullptr;
+  g->d_scen = nullptr;
+  g->d_status = nullptr;
+  g->d_bar = nullptr;
+  g->h_stage = nullptr;
+  g->staged = nullptr;
+  g->cap_stream = nullptr;
+}
+
+int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, std::string* err) {
+  g->prec = prec;
+  g->sched = sched;
+  g->tx = tx;
+  g->ty = ty;
+  g->chunk = chunk;
+  cudaError_t e = cudaMalloc(&g->d_counts, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_bar, sizeof(Bar));
+  if (e == cudaSuccess) e = cudaMemset(g->d_counts, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->d_bar, 0, sizeof(Bar));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->staged, cudaEventDisableTiming);
+  // RTI_BARRIER_SPIN_CYCLES shortens the bounded barrier wait (used to test the timeout path)
+  if (const char* v = std::getenv("RTI_BARRIER_SPIN_CYCLES")) {
+    long long c = std::atoll(v);
+    if (c > 0) g->spin_cycles = c;
+  }
+  if (e == cudaSuccess) {
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid) : persistent_grid<double>(&g->grid);
+  }
+  if (e != cudaSuccess) return cuda_err(err, e, "group setup");
+  return RTI_OK;
+}
+
+template <class T>
+KParams<T> kparams(Group* g, int nsteps) {
+  KParams<T> kp;
+  kp.blk = (const Blk<T>*)g->d_blk;
+  kp.kids = g->d_kids;
+  kp.tiles = g->d_tiles;
+  kp.ntiles = g->d_counts;
+  kp.scen = g->d_scen;
+  kp.status = g->d_status;
+  kp.bar = g->d_bar;
+  kp.nsteps = nsteps;
+  kp.tx = g->tx;
+  kp.ty = g->ty;
+  kp.spin_cycles = g->spin_cycles;
+#ifdef RTI_CHECKED
+  kp.nblk = g->nblk;
+  kp.nkids = g->nkids;
+#endif
+  return kp;
+}
+
+template <class T>
+cudaError_t grow(T** ptr, size_t* cap, size_t need_bytes, bool* moved) {
+  if (need_bytes <= *cap && *ptr) return cudaSuccess;
+  size_t n = std::max(need_bytes, *cap * 2);
+  n = std::max<size_t>(n, 256);
+  cudaFree(*ptr);
+  *ptr = nullptr;
+  cudaError_t e = cudaMalloc((void**)ptr, n);
+  if (e == cudaSuccess) {
+    *cap = n;
+    *moved = true;
+  }
+  return e;
+}
+
+// Rebuild and upload the block table, child lists and tile list of a group (stream-ordered).
+template <class T>
+int group_upload(Group* g, cudaStream_t st, std::string* err) {
+  std::vector<Blk<T>> blks;
+  std::vector<int> kids;
+  std::vector<Tile> tiles;
+  long long cells = 0;
+  for (size_t mi = 0; mi < g->members.size(); ++mi) {
+    rti_handle* h = g->members[mi];
+    const int base = (int)blks.size();
+    const int nb = (int)h->blocks.size();
+    std::vector<std::vector<int>> ch(nb);
+    for (int k = 0; k < nb; ++k)
+      if (h->blocks[k].parent >= 0) ch[h->blocks[k].parent].push_back(k);
+    for (int k = 0; k < nb; ++k) {
+      const int cf = (int)kids.size();
+      for (int c : ch[k]) kids.push_back(base + c);
+      blks.push_back(make_blk<T>(h, k, base, (int)mi, cf, (int)ch[k].size(), g->tx));
+    }
+    for (int k = 0; k < nb; ++k) {
+      const rti_block& d = h->blocks[k];
+      cells += (long long)d.nx * d.ny;
+      for (int ty = 0; ty < h->mem[k].tiles_y; ++ty) {
+        for (int tx = 0; tx < h->mem[k].tiles_x; ++tx) {
+          Tile t;
+          t.blk = base + k;
+          t.x0 = tx * g->tx;
+          t.y0 = ty * g->ty;
+          t.flags = 0;
+          if (t.x0 == 0) t.flags |= kTfWest;
+          if (t.x0 + g->tx >= d.nx) t.flags |= kTfEast;
+          if (t.y0 == 0) t.flags |= kTfSouth;
+          if (t.y0 + g->ty >= d.ny) t.flags |= kTfNorth;
+          for (int c : ch[k]) {  // tile meets the inner ring of a child footprint
+            const rti_block& cd = h->blocks[c];
+            int a0 = cd.i0, a1 = cd.i0 + cd.nx / 3, b0 = cd.j0, b1 = cd.j0 + cd.ny / 3;
+            int x1 = t.x0 + g->tx, y1 = t.y0 + g->ty;
+            bool meets = t.x0 < a1 && a0 < x1 && t.y0 < b1 && b0 < y1;
+            bool inner = t.x0 >= a0 + 1 && x1 <= a1 - 1 && t.y0 >= b0 + 1 && y1 <= b1 - 1;
+            if (meets && !inner) t.flags |= kTfRing;
+          }
+          tiles.push_back(t);
+        }
+      }
+    }
+  }
+  bool moved = false;
+  cudaError_t e = grow(&g->d_blk, &g->cap_blk, blks.size() * sizeof(Blk<T>) + 64, &moved);
+  if (e == cudaSuccess) e = grow(&g->d_kids, &g->cap_kids, kids.size() * sizeof(int) + 64, &moved);
+  if (e == cudaSuccess) e = grow(&g->d_tiles, &g->cap_tiles, tiles.size() * sizeof(Tile) + 64, &moved);
+  if (e == cudaSuccess)
+    e = grow(&g->d_scen, &g->cap_scen, g->members.size() * sizeof(ScenDev) + 64, &moved);
+  if (e != cudaSuccess) return cuda_err(err, e, "device tables");
+  if (moved && g->gexec) {  // the captured graph holds the old pointers
+    cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+    g->graph_tried = false;
+  }
+  const size_t nb_blk = blks.size() * sizeof(Blk<T>);
+  const size_t nb_kids = kids.size() * sizeof(int);
+  const size_t nb_tiles = tiles.size() * sizeof(Tile);
+  const size_t nb_scen = g->members.size() * sizeof(ScenDev);
+  const size_t need = align256(nb_blk) + align256(nb_kids) + align256(nb_tiles) +
+                      align256(nb_scen) + 256;
+  // the previous upload must have left the staging buffer before it is rewritten
+  e = cudaEventSynchronize(g->staged);
+  if (e != cudaSuccess) return cuda_err(err, e, "staging wait");
+  if (need > g->cap_stage) {
+    if (g->h_stage) cudaFreeHost(g->h_stage);
+    g->h_stage = nullptr;
+    e = cudaMallocHost((void**)&g->h_stage, need * 2);
+    if (e != cudaSuccess) return cuda_err(err, e, "pinned staging");
+    g->cap_stage = need * 2;
+  }
+  char* s = g->h_stage;
+  size_t o = 0;
+  auto put = [&](const void* src, size_t n, void* dst) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    std::memcpy(s + o, src, n);
+    cudaError_t r = cudaMemcpyAsync(dst, s + o, n, cudaMemcpyHostToDevice, st);
+    o += align256(n);
+    return r;
+  };
+  std::vector<ScenDev> sc(g->members.size());
+  for (size_t mi = 0; mi < g->members.size(); ++mi) {
+    sc[mi].base = g->members[mi]->base;
+    sc[mi].remaining = g->remaining[mi];
+  }
+  int counts[2] = {(int)tiles.size(), (int)g->members.size()};
+  e = put(blks.data(), nb_blk, g->d_blk);
+  if (e == cudaSuccess) e = put(kids.data(), nb_kids, g->d_kids);
+  if (e == cudaSuccess) e = put(tiles.data(), nb_tiles, g->d_tiles);
+  if (e == cudaSuccess) e = put(sc.data(), nb_scen, g->d_scen);
+  if (e == cudaSuccess) e = put(counts, sizeof(counts), g->d_counts);
+  if (e == cudaSuccess) e = cudaEventRecord(g->staged, st);
+  if (e != cudaSuccess) return cuda_err(err, e, "table upload");
+  g->ntiles = (int)tiles.size();
+  g->nblk = (int)blks.size();
+  g->nkids = (int)kids.size();
+  g->cells = cells;
+  g->dirty = false;
+  return RTI_OK;
+}
+
+int group_upload_any(Group* g, cudaStream_t st, std::string* err) {
+  return g->prec == RTI_FP32 ? group_upload<float>(g, st, err) : group_upload<double>(g, st, err);
+}
+
+int launch_any(Group* g, int nsteps, cudaStream_t st, std::string* err) {
+  cudaError_t e;
+  if (g->prec == RTI_FP32)
+    e = launch_chunk<float>(kparams<float>(g, nsteps), g->sched, g->grid, g->d_counts + 1, st);
+  else
+    e = launch_chunk<double>(kparams<double>(g, nsteps), g->sched, g->grid, g->d_counts + 1, st);
+  if (e != cudaSuccess) return cuda_err(err, e, "chunk launch");
+  return RTI_OK;
+}
+
+int snapshot_any(Group* g, cudaStream_t st, std::string* err) {
+  cudaError_t e = g->prec == RTI_FP32 ? launch_snapshot<float>(kparams<float>(g, 0), g->grid, st)
+                                      : launch_snapshot<double>(kparams<double>(g, 0), g->grid, st);
+  if (e != cudaSuccess) return cuda_err(err, e, "snapshot");
+  return RTI_OK;
+}
+
+// One chunk of a group, through a captured CUDA graph when the capture works.
+int group_chunk(Group* g, cudaStream_t st, std::string* err) {
+  if (!g->graph_tried) {
+    g->graph_tried = true;
+    cudaError_t e = cudaSuccess;
+    if (!g->cap_stream) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      std::string lerr;
+      launch_any(g, g->chunk, g->cap_stream, &lerr);
+      e = cudaStreamEndCapture(g->cap_stream, &graph);
+    }
+    if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&g->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {  // capture unsupported here: launch directly from now on
+      g->gexec = nullptr;
+      cudaGetLastError();
+    }
+  }
+  if (g->gexec) {
+    cudaError_t e = cudaGraphLaunch(g->gexec, st);
+    if (e != cudaSuccess) return cuda_err(err, e, "graph launch");
+    return RTI_OK;
+  }
+  return launch_any(g, g->chunk, st, err);
+}
+
+void advance_mirror(Group* g, int nsteps) {
+  for (size_t mi = 0; mi < g->members.size(); ++mi) {
+    long long d = std::min<long long>(g->remaining[mi], nsteps);
+    if (d < 0) d = 0;
+    g->members[mi]->base += d;
+    g->remaining[mi] -= d;
+  }
+}
+
+int read_status(Group* g, rti_handle* h, std::string* err) {
+  int st_h = 0, st_g = 0;
+  cudaError_t e = cudaMemcpy(&st_h, h->arena + h->off_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && g) e = cudaMemcpy(&st_g, g->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(err, e, "status read");
+  if ((st_h | st_g) & kStTimeout)
+    return set_err(err, RTI_ERR_TIMEOUT, "device barrier wait timed out; state undefined");
+  if (st_h & kStNonFinite) return set_err(err, RTI_ERR_NONFINITE, "non-finite water level");
+  return RTI_OK;
+}
+
+bool bad_block(const rti_handle* h, int k) { return !h || k < 0 || k >= (int)h->blocks.size(); }
+
+// download a pitched plane (ncols x nrows starting at column/row 0) into a host double array
+int download(rti_handle* h, size_t off, int ncols, int nrows, int pitch, bool is_state,
+             double* out, std::string* err) {
+  const size_t es = is_state ? esize(h->prec) : 4;
+  std::vector<char> tmp((size_t)ncols * nrows * es);
+  const char* src = h->arena + off + ((size_t)kYOff * pitch + kXOff) * es;
+  cudaError_t e = cudaMemcpy2D(tmp.data(), (size_t)ncols * es, src, (size_t)pitch * es,
+                               (size_t)ncols * es, (size_t)nrows, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(err, e, "download");
+  h->d2h += (long long)tmp.size();
+  const size_t n = (size_t)ncols * nrows;
+  if (es == 8) std::memcpy(out, tmp.data(), n * 8);
+  else
+    for (size_t c = 0; c < n; ++c) out[c] = (double)((const float*)tmp.data())[c];
+  return RTI_OK;
+}
+
+template <class T>
+int upload_t(rti_handle* h, size_t off, int ncols, int nrows, int pitch, const double* in,
+             std::string* err) {
+  std::vector<T> tmp((size_t)ncols * nrows);
+  for (size_t c = 0; c < tmp.size(); ++c) tmp[c] = (T)in[c];
+  char* dst = h->arena + off + ((size_t)kYOff * pitch + kXOff) * sizeof(T);
+  cudaError_t e = cudaMemcpy2D(dst, (size_t)pitch * sizeof(T), tmp.data(), (size_t)ncols * sizeof(T),
+                               (size_t)ncols * sizeof(T), (size_t)nrows, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_err(err, e, "upload");
+  h->h2d += (long long)(tmp.size() * sizeof(T));
+  return RTI_OK;
+}
+
+int upload(rti_handle* h, size_t off, int ncols, int nrows, int pitch, const double* in,
+           std::string* err) {
+  return h->prec == RTI_FP32 ? upload_t<float>(h, off, ncols, nrows, pitch, in, err)
+                             : upload_t<double>(h, off, ncols, nrows, pitch, in, err);
+}
+
+int wait_handle(rti_handle* h) {
+  cudaError_t e = cudaEventSynchronize(h->done);
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "wait");
+  return RTI_OK;
+}
+
+// initial level and outputs of block k on the host, in the state precision
+template <class T>
+int init_block_t(rti_handle* h, int k, const double* dz, const double* host_h) {
+  const rti_block& d = h->blocks[k];
+  const BlkMem& m = h->mem[k];
+  const size_t n = (size_t)d.nx * d.ny;
+  std::vector<double> hd;
+  if (!host_h) {
+    hd.resize(n);
+    int rc = download(h, m.h, d.nx, d.ny, m.pitch, true, hd.data(), &h->err);
+    if (rc) return rc;
+  }
+  const double* hsrc = host_h ? host_h : hd.data();
+  std::vector<T> eta(n), emax(n);
+  std::vector<int> arr(n);
+  const T eps = (T)h->params.dry_eps, thr = (T)h->params.arrival_thr;
+  for (size_t c = 0; c < n; ++c) {
+    const double hh = (double)(T)hsrc[c];
+    double e0;
+    if (hh > 0) {
+      e0 = dz ? dz[c] : 0.0;
+      if (e0 < -hh) e0 = -hh;
+    } else {
+      e0 = -hh;
+    }
+    T e = (T)e0;
+    const T ht = (T)hh;
+    eta[c] = e;
+    emax[c] = (T)kNeverWet;
+    arr[c] = -1;
+    if (ht + e > eps && e > emax[c]) {
+      if (emax[c] < thr && e >= thr) arr[c] = 0;
+      emax[c] = e;
+    }
+  }
+  const size_t es = sizeof(T);
+  auto put = [&](size_t off, const void* src, size_t el) -> cudaError_t {
+    char* dst = h->arena + off + ((size_t)kYOff * m.pitch + kXOff) * el;
+    h->h2d += (long long)(n * el);
+    return cudaMemcpy2D(dst, (size_t)m.pitch * el, src, (size_t)d.nx * el, (size_t)d.nx * el,
+                        (size_t)d.ny, cudaMemcpyHostToDevice);
+  };
+  const size_t plane = (size_t)m.pitch * m.rows;
+  cudaError_t e = put(m.eta[0], eta.data(), es);
+  if (e == cudaSuccess) e = put(m.emax, emax.data(), es);
+  if (e == cudaSuccess) e = put(m.arr, arr.data(), 4);
+  for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = cudaMemset(h->arena + m.M[s], 0, plane * es);
+  for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = cudaMemset(h->arena + m.N[s], 0, plane * es);
+  if (e == cudaSuccess)
+    e = cudaMemset(h->arena + m.budget, 0, (size_t)m.tiles_x * m.tiles_y * 4 * sizeof(double));
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "initial state");
+  return RTI_OK;
+}
+
+}  // namespace
+
+// ============================================================================== C ABI
+extern "C" {
+
+const char* rti_error_string(int code) {
+  switch (code) {
+    case RTI_OK: return "ok";
+    case RTI_ERR_INVALID_ARG: return "invalid argument";
+    case RTI_ERR_CFL: return "CFL condition violated (Eq. 4)";
+    case RTI_ERR_NESTING: return "invalid nesting";
+    case RTI_ERR_OOM: return "out of device memory";
+    case RTI_ERR_NONFINITE: return "non-finite water level";
+    case RTI_ERR_TIMEOUT: return "device barrier timeout";
+    case RTI_ERR_CUDA: return "CUDA error";
+    case RTI_ERR_STATE: return "call not allowed in this state";
+    default: return "unknown error";
+  }
+}
+
+// message of the last rti_create that failed on this thread
+static thread_local std::string t_create_err;
+
+const char* rti_last_error(const rti_handle* h) { return h ? h->err.c_str() : t_create_err.c_str(); }
+
+int rti_footprint(const rti_block* blocks, int nblocks, const rti_params* params, size_t* bytes) {
+  std::string why;
+  if (!bytes) return RTI_ERR_INVALID_ARG;
+  int rc = validate(blocks, nblocks, params, &why);
+  if (rc) return rc;
+  const int tx = params->tile_x ? params->tile_x : kDefaultTx;
+  const int ty = params->tile_y ? params->tile_y : kDefaultTy;
+  *bytes = plan_layout(blocks, nblocks, params->precision, tx, ty, nullptr, nullptr);
+  return RTI_OK;
+}
+
+int rti_create(const rti_block* blocks, int nblocks, const double* const* bathy,
+               const float* const* manning, const rti_params* params, void* device_mem,
+               size_t device_bytes, rti_handle** out) {
+  if (!out) return RTI_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  int rc = validate(blocks, nblocks, params, &why);
+  if (rc) return rc;
+  if (!bathy || !manning) return RTI_ERR_INVALID_ARG;
+  for (int k = 0; k < nblocks; ++k)
+    if (!bathy[k] || !manning[k]) return RTI_ERR_INVALID_ARG;
+  for (int k = 0; k < nblocks; ++k) {  // Eq. 4 with the block's own h_max
+    double hmax = 0.0;
+    const size_t n = (size_t)blocks[k].nx * blocks[k].ny;
+    for (size_t c = 0; c < n; ++c) {
+      if (!std::isfinite(bathy[k][c]) || !std::isfinite(manning[k][c])) return RTI_ERR_INVALID_ARG;
+      hmax = std::max(hmax, bathy[k][c]);
+    }
+    if (blocks[k].dx / params->dt < std::sqrt(2.0 * params->g * hmax)) return RTI_ERR_CFL;
+  }
+  if (device_mem && ((uintptr_t)device_mem & 255)) return RTI_ERR_INVALID_ARG;
+  rti_handle* h = new (std::nothrow) rti_handle();
+  if (!h) return RTI_ERR_OOM;
+  h->prec = params->precision;
+  h->params = *params;
+  h->params.tile_x = params->tile_x ? params->tile_x : kDefaultTx;
+  h->params.tile_y = params->tile_y ? params->tile_y : kDefaultTy;
+  h->blocks.assign(blocks, blocks + nblocks);
+  h->arena_bytes = plan_layout(blocks, nblocks, h->prec, h->params.tile_x, h->params.tile_y,
+                               &h->mem, &h->off_status);
+  for (int k = 0; k < nblocks; ++k) h->cells += (long long)blocks[k].nx * blocks[k].ny;
+  cudaError_t e = cudaSuccess;
+  if (device_mem) {
+    if (device_bytes < h->arena_bytes) {
+      delete h;
+      return RTI_ERR_OOM;
+    }
+    h->arena = (char*)device_mem;
+  } else {
+    e = cudaMalloc((void**)&h->arena, h->arena_bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return e == cudaErrorMemoryAllocation ? RTI_ERR_OOM : RTI_ERR_CUDA;
+    }
+    h->own = true;
+  }
+  auto fail = [&](int code) {
+    cudaError_t last = cudaGetLastError();
+    t_create_err = h->err.empty() ? std::string("rti_create: ") + cuda_name(last) : h->err;
+    rti_destroy(h);
+    return code;
+  };
+  e = cudaMemset(h->arena, 0, h->arena_bytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cuda_err(&h->err, e, "arena setup");
+    return fail(RTI_ERR_CUDA);
+  }
+  // bathymetry and Manning n into the pitched arrays; sum of h per block for the budget
+  h->sum_h.assign(nblocks, 0.0);
+  for (int k = 0; k < nblocks; ++k) {
+    const rti_block& d = blocks[k];
+    const BlkMem& m = h->mem[k];
+    const size_t n = (size_t)d.nx * d.ny;
+    rc = upload(h, m.h, d.nx, d.ny, m.pitch, bathy[k], &h->err);
+    if (rc) return fail(rc);
+    double s = 0.0;
+    for (size_t c = 0; c < n; ++c)
+      s += h->prec == RTI_FP32 ? (double)(float)bathy[k][c] : bathy[k][c];
+    h->sum_h[k] = s;
+    char* dst = h->arena + m.man + ((size_t)kYOff * m.pitch + kXOff) * 4;
+    e = cudaMemcpy2D(dst, (size_t)m.pitch * 4, manning[k], (size_t)d.nx * 4, (size_t)d.nx * 4,
+                     (size_t)d.ny, cudaMemcpyHostToDevice);
+    h->h2d += (long long)n * 4;
+    if (e != cudaSuccess) {
+      cuda_err(&h->err, e, "manning upload");
+      return fail(RTI_ERR_CUDA);
+    }
+  }
+  h->self = new (std::nothrow) Group();
+  if (!h->self) return fail(RTI_ERR_OOM);
+  rc = group_init(h->self, h->prec, params->schedule, h->params.tile_x, h->params.tile_y, 1, &h->err);
+  if (rc) return fail(rc);
+  h->self->members.push_back(h);
+  h->self->remaining.push_back(0);
+  rc = group_upload_any(h->self, 0, &h->err);
+  if (rc) return fail(rc);
+  for (int k = 0; k < nblocks; ++k) {
+    rc = h->prec == RTI_FP32 ? init_block_t<float>(h, k, nullptr, bathy[k])
+                             : init_block_t<double>(h, k, nullptr, bathy[k]);
+    if (rc) return fail(rc);
+  }
+  rc = snapshot_any(h->self, 0, &h->err);
+  if (rc) return fail(rc);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cuda_err(&h->err, e, "create sync");
+    return fail(RTI_ERR_CUDA);
+  }
+  *out = h;
+  return RTI_OK;
+}
+
+int rti_set_initial_uplift(rti_handle* h, int block, const double* dz) {
+  if (bad_block(h, block)) return RTI_ERR_INVALID_ARG;
+  if (h->batch) return set_err(&h->err, RTI_ERR_STATE, "handle is in a batch");
+  int rc = wait_handle(h);
+  if (rc) return rc;
+  const size_t es = esize(h->prec);
+  if (h->base & 1) {  // move the other blocks' current level to parity 0
+    for (size_t k = 0; k < h->blocks.size(); ++k) {
+      const BlkMem& m = h->mem[k];
+      const size_t plane = (size_t)m.pitch * m.rows * es;
+      cudaError_t e = cudaMemcpy(h->arena + m.eta[0], h->arena + m.eta[1], plane, cudaMemcpyDeviceToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(h->arena + m.M[0], h->arena + m.M[1], plane, cudaMemcpyDeviceToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(h->arena + m.N[0], h->arena + m.N[1], plane, cudaMemcpyDeviceToDevice);
+      if (e != cudaSuccess) return cuda_err(&h->err, e, "parity reset");
+    }
+  }
+  h->base = 0;
+  rc = h->prec == RTI_FP32 ? init_block_t<float>(h, block, dz, nullptr)
+                           : init_block_t<double>(h, block, dz, nullptr);
+  if (rc) return rc;
+  cudaError_t e = cudaMemset(h->arena + h->off_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->self->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "status reset");
+  h->self->remaining[0] = 0;
+  h->self->dirty = true;
+  rc = group_upload_any(h->self, 0, &h->err);
+  if (rc) return rc;
+  rc = snapshot_any(h->self, 0, &h->err);
+  if (rc) return rc;
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "initial condition");
+  return RTI_OK;
+}
+
+int rti_step(rti_handle* h, int nsteps, void* stream) {
+  if (!h || nsteps < 0) return RTI_ERR_INVALID_ARG;
+  if (h->batch) return set_err(&h->err, RTI_ERR_STATE, "handle is stepped by its batch");
+  if (nsteps == 0) return RTI_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Group* g = h->self;
+  k_set_scen<<<1, 1, 0, st>>>(g->d_scen, 0, h->base, nsteps);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "step setup");
+  g->remaining[0] = nsteps;
+  int rc = launch_any(g, nsteps, st, &h->err);
+  if (rc) return rc;
+  advance_mirror(g, nsteps);
+  e = cudaEventRecord(h->done, st);
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "event");
+  return RTI_OK;
+}
+
+int rti_sync(rti_handle* h) {
+  if (!h) return RTI_ERR_INVALID_ARG;
+  int rc = wait_handle(h);
+  if (rc) return rc;
+  if (h->batch) {
+    cudaError_t e = cudaEventSynchronize(h->batch->done);
+    if (e != cudaSuccess) return cuda_err(&h->err, e, "wait");
+    return read_status(&h->batch->g, h, &h->err);
+  }
+  return read_status(h->self, h, &h->err);
+}
+
+static int sync_for_read(rti_handle* h) {
+  int rc = wait_handle(h);
+  if (rc) return rc;
+  if (h->batch) {
+    cudaError_t e = cudaEventSynchronize(h->batch->done);
+    if (e != cudaSuccess) return cuda_err(&h->err, e, "wait");
+  }
+  return RTI_OK;
+}
+
+int rti_get_state(rti_handle* h, int block, double* eta, double* M, double* N) {
+  if (bad_block(h, block)) return RTI_ERR_INVALID_ARG;
+  int rc = sync_for_read(h);
+  if (rc) return rc;
+  const rti_block& d = h->blocks[block];
+  const BlkMem& m = h->mem[block];
+  const int p = (int)(h->base & 1);
+  if (d.parent >= 0 && (M || N)) {  // a child's edge fluxes are defined by its parent
+    Group* g = h->self;
+    cudaError_t e = g->prec == RTI_FP32
+                        ? launch_fill_edges<float>(kparams<float>(g, 0), g->grid, p, 0)
+                        : launch_fill_edges<double>(kparams<double>(g, 0), g->grid, p, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_err(&h->err, e, "edge fluxes");
+  }
+  if (eta && (rc = download(h, m.eta[p], d.nx, d.ny, m.pitch, true, eta, &h->err))) return rc;
+  if (M && (rc = download(h, m.M[p], d.nx + 1, d.ny, m.pitch, true, M, &h->err))) return rc;
+  if (N && (rc = download(h, m.N[p], d.nx, d.ny + 1, m.pitch, true, N, &h->err))) return rc;
+  return RTI_OK;
+}
+
+int rti_set_state(rti_handle* h, int block, const double* eta, const double* M, const double* N) {
+  if (bad_block(h, block)) return RTI_ERR_INVALID_ARG;
+  if (h->batch) return set_err(&h->err, RTI_ERR_STATE, "handle is in a batch");
+  int rc = wait_handle(h);
+  if (rc) return rc;
+  const rti_block& d = h->blocks[block];
+  const BlkMem& m = h->mem[block];
+  const int p = (int)(h->base & 1);
+  if (eta && (rc = upload(h, m.eta[p], d.nx, d.ny, m.pitch, eta, &h->err))) return rc;
+  if (M && (rc = upload(h, m.M[p], d.nx + 1, d.ny, m.pitch, M, &h->err))) return rc;
+  if (N && (rc = upload(h, m.N[p], d.nx, d.ny + 1, m.pitch, N, &h->err))) return rc;
+  rc = snapshot_any(h->self, 0, &h->err);
+  if (rc) return rc;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "set state");
+  return RTI_OK;
+}
+
+static int get_out(rti_handle* h, int block, double* out, int kind) {
+  if (bad_block(h, block) || !out) return RTI_ERR_INVALID_ARG;
+  int rc = sync_for_read(h);
+  if (rc) return rc;
+  const rti_block& d = h->blocks[block];
+  const BlkMem& m = h->mem[block];
+  const size_t n = (size_t)d.nx * d.ny;
+  if (kind == 2) {  // arrival
+    std::vector<int> a(n);
+    char* src = h->arena + m.arr + ((size_t)kYOff * m.pitch + kXOff) * 4;
+    cudaError_t e = cudaMemcpy2D(a.data(), (size_t)d.nx * 4, src, (size_t)m.pitch * 4,
+                                 (size_t)d.nx * 4, (size_t)d.ny, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(&h->err, e, "arrival");
+    h->d2h += (long long)n * 4;
+    for (size_t c = 0; c < n; ++c) out[c] = a[c] < 0 ? -1.0 : (double)a[c] * h->params.dt;
+    return RTI_OK;
+  }
+  std::vector<double> em(n);
+  rc = download(h, m.emax, d.nx, d.ny, m.pitch, true, em.data(), &h->err);
+  if (rc) return rc;
+  if (kind == 1) {  // max height
+    for (size_t c = 0; c < n; ++c) out[c] = em[c] == kNeverWet ? NAN : em[c];
+    return RTI_OK;
+  }
+  std::vector<double> hd(n);
+  rc = download(h, m.h, d.nx, d.ny, m.pitch, true, hd.data(), &h->err);
+  if (rc) return rc;
+  for (size_t c = 0; c < n; ++c) out[c] = em[c] == kNeverWet ? 0.0 : hd[c] + em[c];
+  return RTI_OK;
+}
+
+int rti_get_max_depth(rti_handle* h, int block, double* out) { return get_out(h, block, out, 0); }
+int rti_get_max_height(rti_handle* h, int block, double* out) { return get_out(h, block, out, 1); }
+int rti_get_arrival_time(rti_handle* h, int block, double* out) { return get_out(h, block, out, 2); }
+
+int rti_get_budget(rti_handle* h, int block, double out[4]) {
+  if (bad_block(h, block) || !out) return RTI_ERR_INVALID_ARG;
+  int rc = sync_for_read(h);
+  if (rc) return rc;
+  const BlkMem& m = h->mem[block];
+  const size_t nt = (size_t)m.tiles_x * m.tiles_y;
+  std::vector<double> s(nt * 4);
+  cudaError_t e = cudaMemcpy(s.data(), h->arena + m.budget, nt * 4 * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "budget");
+  double acc[4] = {0, 0, 0, 0};
+  for (size_t t = 0; t < nt; ++t)
+    for (int q = 0; q < 4; ++q) acc[q] += s[4 * t + q];
+  const double dx = h->blocks[block].dx;
+  out[0] = (h->sum_h[block] + acc[0]) * (dx * dx);
+  out[1] = acc[2];
+  out[2] = acc[1];
+  out[3] = acc[3];
+  return RTI_OK;
+}
+
+int rti_get_transfer_bytes(const rti_handle* h, long long* h2d, long long* d2h) {
+  if (!h || !h2d || !d2h) return RTI_ERR_INVALID_ARG;
+  *h2d = h->h2d;
+  *d2h = h->d2h;
+  return RTI_OK;
+}
+
+#ifdef RTI_CHECKED
+// Checked builds only: the first out-of-range kernel access of the binary64 module
+// (out8[0..7]) and of the binary32 module (out8[8..15]): code, index, extent, ..., CTA.
+extern "C" int rti_debug_check(int* out16) {
+  cudaError_t e = rti::debug_check_fp64(out16);
+  if (e == cudaSuccess) e = rti::debug_check_fp32(out16 + 8);
+  return e == cudaSuccess ? RTI_OK : RTI_ERR_CUDA;
+}
+#endif
+
+long long rti_steps_done(rti_handle* h) {
+  if (!h) return -1;
+  if (sync_for_read(h)) return -1;
+  return h->base;
+}
+int rti_num_blocks(const rti_handle* h) { return h ? (int)h->blocks.size() : 0; }
+long long rti_num_cells(const rti_handle* h) { return h ? h->cells : 0; }
+
+void rti_destroy(rti_handle* h) {
+  if (!h) return;
+  if (h->batch) rti_batch_remove(h->batch, h);
+  if (h->done) cudaEventSynchronize(h->done);
+  if (h->self) {
+    free_group_dev(h->self);
+    delete h->self;
+  }
+  if (h->done) cudaEventDestroy(h->done);
+  if (h->own && h->arena) cudaFree(h->arena);
+  delete h;
+}
+
+// ------------------------------------------------------------------------------ batches
+int rti_batch_create(int precision, int schedule, int chunk_steps, rti_batch** out) {
+  if (!out || chunk_steps <= 0 || (precision != RTI_FP32 && precision != RTI_FP64) ||
+      (schedule != RTI_SCHED_PERSISTENT && schedule != RTI_SCHED_PER_PASS))
+    return RTI_ERR_INVALID_ARG;
+  rti_batch* b = new (std::nothrow) rti_batch();
+  if (!b) return RTI_ERR_OOM;
+  int rc = group_init(&b->g, precision, schedule, kDefaultTx, kDefaultTy, chunk_steps, &b->err);
+  if (rc == RTI_OK && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
+    rc = RTI_ERR_CUDA;
+  if (rc) {
+    free_group_dev(&b->g);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return RTI_OK;
+}
+
+int rti_batch_add(rti_batch* b, rti_handle* h, long long nsteps) {
+  if (!b || !h || nsteps < 0) return RTI_ERR_INVALID_ARG;
+  if (h->batch) return set_err(&h->err, RTI_ERR_STATE, "handle already in a batch");
+  if (h->prec != b->g.prec || h->params.tile_x != b->g.tx || h->params.tile_y != b->g.ty)
+    return set_err(&h->err, RTI_ERR_INVALID_ARG, "precision or tile shape differs from the batch");
+  int rc = wait_handle(h);
+  if (rc) return rc;
+  b->g.members.push_back(h);
+  b->g.remaining.push_back(nsteps);
+  b->g.dirty = true;
+  h->batch = b;
+  return RTI_OK;
+}
+
+int rti_batch_remove(rti_batch* b, rti_handle* h) {
+  if (!b || !h || h->batch != b) return RTI_ERR_INVALID_ARG;
+  cudaEventSynchronize(b->done);  // the member's kernels must be finished
+  for (size_t i = 0; i < b->g.members.size(); ++i) {
+    if (b->g.members[i] == h) {
+      b->g.members.erase(b->g.members.begin() + i);
+      b->g.remaining.erase(b->g.remaining.begin() + i);
+      break;
+    }
+  }
+  h->batch = nullptr;
+  b->g.dirty = true;
+  // the handle's own group keeps stepping it from where the batch left it
+  h->self->remaining[0] = 0;
+  return RTI_OK;
+}
+
+int rti_batch_step(rti_batch* b, void* stream) {
+  if (!b) return RTI_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (b->g.dirty) {
+    int rc = group_upload_any(&b->g, st, &b->err);
+    if (rc) return rc;
+  }
+  if (b->g.members.empty()) return RTI_OK;
+  int rc = group_chunk(&b->g, st, &b->err);
+  if (rc) return rc;
+  advance_mirror(&b->g, b->g.chunk);
+  cudaError_t e = cudaEventRecord(b->done, st);
+  if (e != cudaSuccess) return cuda_err(&b->err, e, "event");
+  return RTI_OK;
+}
+
+long long rti_batch_remaining(rti_batch* b, rti_handle* h) {
+  if (!b) return -1;
+  for (size_t i = 0; i < b->g.members.size(); ++i)
+    if (b->g.members[i] == h) return b->g.remaining[i];
+  return -1;
+}
+
+int rti_batch_sync(rti_batch* b) {
+  if (!b) return RTI_ERR_INVALID_ARG;
+  cudaError_t e = cudaEventSynchronize(b->done);
+  if (e != cudaSuccess) return cuda_err(&b->err, e, "wait");
+  for (rti_handle* h : b->g.members) {
+    int rc = read_status(&b->g, h, &h->err);
+    if (rc) return rc;
+  }
+  return RTI_OK;
+}
+
+void rti_batch_destroy(rti_batch* b) {
+  if (!b) return;
+  cudaEventSynchronize(b->done);
+  for (rti_handle* h : b->g.members) h->batch = nullptr;
+  free_group_dev(&b->g);
+  if (b->done) cudaEventDestroy(b->done);
+  delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// rti_instantiate.cuh -- launchers for one precision RTI_T (included once per .cu).
+#include "rti_kernels.cuh"
+#include "rti_launch.h"
+
+namespace rti {
+
+template <>
+cudaError_t persistent_grid<RTI_T>(int* grid) {
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<RTI_T>, 256, 0);
+  if (e == cudaSuccess) *grid = sms * (per > 0 ? per : 1);
+  return e;
+}
+
+template <>
+cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid,
+                                const int* nscen, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  const dim3 blk(32, 8);
+  if (schedule == 0) {
+    e = cudaMemsetAsync(kp.bar, 0, sizeof(Bar), st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = blk;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_persistent<RTI_T>, kp);
+  } else {
+    for (int s = 0; s < kp.nsteps && e == cudaSuccess; ++s) {
+      k_pass_a<RTI_T><<<grid, blk, 0, st>>>(kp, s);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      k_pass_b<RTI_T><<<grid, blk, 0, st>>>(kp, s);
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) return e;
+  k_advance<<<1, 256, 0, st>>>(kp.scen, nscen, kp.nsteps);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_snapshot<RTI_T>(const KParams<RTI_T>& kp, int grid, cudaStream_t st) {
+  k_snapshot<RTI_T><<<grid, dim3(32, 8), 0, st>>>(kp);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_fill_edges<RTI_T>(const KParams<RTI_T>& kp, int grid, int parity,
+                                     cudaStream_t st) {
+  k_fill_edges<RTI_T><<<grid, dim3(32, 8), 0, st>>>(kp, parity);
+  return cudaGetLastError();
+}
+
+}  // namespace rti

@@ -1,0 +1,91 @@
+// rti_layout.h -- device data layout shared by the host library and the kernels.
+//
+// Every field of a block lives in its own pitched 2-D array with a margin: element
+// (column c, row r) is at (r + kYOff) * pitch + (c + kXOff). Cells use columns
+// 0..nx-1 and rows 0..ny-1; x-faces (M) columns 0..nx; y-faces (N) rows 0..ny.
+// The margin keeps every stencil read of the kernels inside the allocation; the
+// kernels still test indices for the numerics. Rows start on 128-byte boundaries.
+#pragma once
+
+#include <stdint.h>
+
+namespace rti {
+
+constexpr int kXOff = 4;       // margin columns before column 0
+constexpr int kYOff = 2;       // margin rows before row 0 and after row ny
+constexpr int kPitchAlign = 32; // elements
+constexpr double kNeverWet = -1.0e30;
+
+enum : int { kBcWall = 0, kBcRadiation = 1 };
+enum : int { kStNonFinite = 1, kStTimeout = 2 };
+// tile flags
+enum : int { kTfWest = 1, kTfEast = 2, kTfSouth = 4, kTfNorth = 8, kTfRing = 16 };
+
+inline int pitch_for(int nx) {
+  int w = kXOff + nx + 1 + 4;
+  return (w + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+}
+inline long long rows_for(int ny) { return (long long)ny + 1 + 2 * kYOff; }
+
+// Per-block descriptor in device memory. T is the state precision.
+template <class T>
+struct Blk {
+  T* eta[2];  // ping-pong water level (deviation from still water)
+  T* M[2];    // ping-pong x-fluxes
+  T* N[2];    // ping-pong y-fluxes
+  const T* h; // still-water depth
+  const float* man;
+  T* emax;    // max eta over wet instants (kNeverWet until wet)
+  int* arr;   // arrival step, -1 if never
+  int nx, ny, pitch, parent; // parent: index in the batch block table, -1 for a root
+  int i0, j0;                // child origin in parent cells
+  int child_first, child_count; // children: kids[child_first .. +child_count)
+  int bc[4];
+  int scen;   // scenario slot (ScenDev index)
+  int is_child;
+  int tiles_x;     // tiles along x (tile slot = ty_index * tiles_x + tx_index)
+  double* budget;  // 4 doubles per tile of this block: sum(eta) snapshot, clip, outflow, ring
+  int* status;     // the owning handle's device status word
+  // constants in the state precision (all exactly the values the oracle uses in FP64)
+  T dtdx, dt, g, cfric /* 0.5*dt*g */, eps, thr, dx, q4dt /* 4*dt */;
+  // binary64 constants for the nesting sums and the budget
+  double dx2, vol /* dt*dx */, eps_d;
+#ifdef RTI_CHECKED
+  const char* lo;  // the owning handle's arena, for the range-checked build
+  const char* hi;
+#endif
+};
+
+struct ScenDev {
+  long long base;    // steps completed before this chunk
+  long long remaining; // steps left as of the start of this chunk
+};
+
+struct Bar {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// One tile: cells [x0, x0+tx) x [y0, y0+ty) of block `blk`.
+struct Tile {
+  int blk, x0, y0, flags;
+};
+
+template <class T>
+struct KParams {
+  const Blk<T>* blk;
+  const int* kids;
+  const Tile* tiles;
+  const int* ntiles;   // device-resident tile count (patched between chunks)
+  ScenDev* scen;
+  int* status;         // group status (barrier timeout)
+  Bar* bar;
+  int nsteps;
+  int tx, ty;          // tile shape in cells
+  long long spin_cycles;
+#ifdef RTI_CHECKED
+  int nblk, nkids;     // table sizes, for the range-checked build
+#endif
+};
+
+}  // namespace rti

@@ -19,3 +19,12 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def rti():
+    """The Python binding with the CUDA library built in-tree."""
+    from paper_2408_07609_gb300 import build, rti as mod
+
+    build.build()
+    return mod

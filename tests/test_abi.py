@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every entry point include/rti.h declares, and
+its host-side validation works without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "rti.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rti_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(rti):
+    L = C.CDLL(rti.LIB)
+    names = declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    # the binding wraps every one of them
+    bound = set(re.findall(r'"(rti_\w+)"', open(rti.__file__).read()))
+    assert set(names) <= bound
+
+
+def blk(**kw):
+    d = dict(level=1, parent=-1, nx=30, ny=30, i0=0, j0=0, dx=100.0, bc=(0, 0, 0, 0))
+    d.update(kw)
+    return d
+
+
+def test_footprint_and_validation_on_host(rti):
+    p = rti.make_params(dt=0.5)
+    fp = rti.footprint([blk()], p)
+    assert fp > 30 * 30 * 8 * 8
+    assert rti.footprint([blk()], rti.make_params(dt=0.5, precision=rti.FP32)) < fp
+    bad = [blk(), blk(level=2, parent=0, nx=30, ny=30, i0=2, j0=3, dx=100 / 3)]
+    with pytest.raises(rti.RtiError) as e:
+        rti.footprint(bad, p)
+    assert e.value.code == -3
+    with pytest.raises(rti.RtiError) as e:
+        rti.footprint([blk(nx=2)], p)
+    assert e.value.code == -1
+    with pytest.raises(rti.RtiError) as e:
+        rti.footprint([blk()], rti.make_params(dt=0.5, tile=(48, 16)))
+    assert e.value.code == -1
+
+
+def test_create_rejects_cfl_before_any_device_call(rti):
+    """Eq. 4 per block: dx/dt >= sqrt(2 g h_max). Checked on the host first."""
+    h = np.full((30, 30), 1000.0)
+    n = np.zeros((30, 30), np.float32)
+    with pytest.raises(rti.RtiError) as e:
+        rti.Handle([blk()], [h], [n], dt=1.0)
+    assert e.value.code == -2
+    with pytest.raises(rti.RtiError) as e:
+        rti.Handle([blk()], [np.full((30, 30), np.nan)], [n], dt=0.1)
+    assert e.value.code == -1
+
+
+def test_error_strings(rti):
+    L = rti.lib()
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert L.rti_error_string(code)

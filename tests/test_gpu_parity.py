@@ -1,0 +1,197 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded synthetic inputs.
+
+Binary64 bar: max|gpu - oracle| / max|oracle| <= 1e-12 per field and block (the
+kernels round like the oracle; only the library cbrt may differ by an ulp).
+Binary32 bar: the accuracy stated for the forecast outputs (max |d eta| in metres,
+wet/dry mismatch, arrival error); see test_fp32_accuracy_report.
+"""
+import numpy as np
+import pytest
+
+from paper_2408_07609_gb300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+def relerr(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / scale if scale > 0 else np.abs(a - b).max()
+
+
+def compare_fp64(h, o, nblocks, tol=TOL64, outputs=True):
+    for k in range(nblocks):
+        ge, gM, gN = h.get_state(k)
+        oe, oM, oN = o.get_state(k)
+        for name, a, b in (("eta", ge, oe), ("M", gM, oM), ("N", gN, oN)):
+            assert relerr(a, b) <= tol, (k, name, relerr(a, b))
+        if outputs:
+            gh, oh = h.max_height(k), o.max_height(k)
+            assert np.array_equal(np.isnan(gh), np.isnan(oh)), k
+            m = ~np.isnan(oh)
+            if m.any():
+                assert relerr(gh[m], oh[m]) <= tol
+            ga, oa = h.arrival_time(k), o.arrival_time(k)
+            # arrival is a threshold crossing: equal except where the level sits within
+            # rounding of the threshold at the crossing step
+            assert (ga != oa).mean() <= 1e-4, k
+        gb, ob = h.budget(k), o.budget(k)
+        assert abs(gb["volume"] - ob["volume"]) <= 1e-12 * abs(ob["volume"])
+        for key in ("outflow", "clip", "ring"):
+            assert abs(gb[key] - ob[key]) <= 1e-9 * max(1.0, abs(ob[key])), key
+
+
+def run_pair(rti, oracle_mod, sc, steps, precision=0, schedule=0, tile=(0, 0)):
+    h = rti.Handle.from_scenario(sc, precision=precision, schedule=schedule, tile=tile)
+    o = oracle_mod.from_scenario(sc)
+    h.step(steps)
+    h.sync()
+    o.step(steps)
+    return h, o
+
+
+def test_single_grid_fp64_full_run(rti, oracle_mod):
+    """256 x 256, dx 1000 m, 1800 steps: radiation west, coast east (wet/dry), friction."""
+    sc = S.config1()
+    h, o = run_pair(rti, oracle_mod, sc, sc.steps)
+    assert h.steps_done == sc.steps
+    compare_fp64(h, o, 1)
+    assert (o.arrival_time(0) > 0).sum() > 1000
+
+
+def test_ragged_single_grid_fp64(rti, oracle_mod):
+    """Sizes that are not multiples of the tile, several tiles, both schedules."""
+    sc = S.config1(nx=203, ny=157, steps=400)
+    for sched in (0, 1):
+        h, o = run_pair(rti, oracle_mod, sc, sc.steps, schedule=sched)
+        compare_fp64(h, o, 1)
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (64, 16), (128, 8)])
+def test_tile_shapes_bitwise_equal(rti, oracle_mod, tile):
+    sc = S.config1(nx=150, ny=90, steps=200)
+    h, o = run_pair(rti, oracle_mod, sc, sc.steps, tile=tile)
+    compare_fp64(h, o, 1)
+
+
+def test_three_level_nest_fp64(rti, oracle_mod):
+    """600^2 / 450^2 / 450^2 at 810 / 270 / 90 m: the coarse-to-fine pull, the
+    fine-to-coarse ring recompute and wet/dry on a fractal coast."""
+    sc = S.config2(steps=300)
+    h, o = run_pair(rti, oracle_mod, sc, sc.steps)
+    compare_fp64(h, o, 3)
+    assert o.budget(0)["ring"] != 0.0
+
+
+def test_lake_at_rest_gpu_bitwise(rti):
+    sc = S.config2(steps=0)
+    sc.uplift = [None] * len(sc.blocks)
+    h = rti.Handle.from_scenario(sc)
+    h.step(500)
+    for k in range(3):
+        e, M, N = h.get_state(k)
+        assert np.array_equal(e, np.where(sc.bathy[k] > 0, 0.0, -sc.bathy[k]))
+        assert not M.any() and not N.any()
+
+
+def test_batch_of_grids_fp64_matches_oracle_and_alone(rti, oracle_mod):
+    """Grids of different sizes and dt stepped together in one persistent launch:
+    each equals the oracle, and equals the same grid stepped alone, bitwise."""
+    grids = S.config3(count=64, steps=120)
+    pick = sorted(grids, key=lambda s: s.cells)[:6]
+    b = rti.Batch(precision=0, chunk_steps=40)
+    hs = []
+    for sc in pick:
+        h = rti.Handle.from_scenario(sc)
+        b.add(h, sc.steps)
+        hs.append(h)
+    while any(b.remaining(h) > 0 for h in hs):
+        b.step()
+    b.sync()
+    for sc, h in zip(pick, hs):
+        o = oracle_mod.from_scenario(sc)
+        o.step(sc.steps)
+        assert h.steps_done == sc.steps
+        compare_fp64(h, o, 1)
+        alone = rti.Handle.from_scenario(sc)
+        alone.step(sc.steps)
+        for a, c in zip(h.get_state(0), alone.get_state(0)):
+            assert np.array_equal(a, c)
+    b.close()
+
+
+def test_members_with_different_lengths_stop_on_their_own(rti):
+    grids = S.config3(count=64, steps=10)
+    pick = sorted(grids, key=lambda s: s.cells)[:3]
+    b = rti.Batch(precision=1, chunk_steps=7)
+    hs = [rti.Handle.from_scenario(sc, precision=1) for sc in pick]
+    for h, n in zip(hs, (5, 13, 21)):
+        b.add(h, n)
+    for _ in range(3):
+        b.step()
+    b.sync()
+    assert [h.steps_done for h in hs] == [5, 13, 21]
+    assert [b.remaining(h) for h in hs] == [0, 0, 0]
+
+
+def test_full_size_five_level_fp64_one_step(rti, oracle_mod):
+    """The 46.65 M-cell 5-level hierarchy in the benchmark's launch configuration,
+    two steps, every cell of every block against the oracle."""
+    sc = S.config4(steps=2)
+    h, o = run_pair(rti, oracle_mod, sc, 2)
+    compare_fp64(h, o, len(sc.blocks), outputs=False)
+
+
+def test_nonfinite_level_is_reported(rti):
+    sc = S.config1(nx=64, ny=64, steps=1)
+    h = rti.Handle.from_scenario(sc)
+    e, M, N = h.get_state(0)
+    e[10, 10] = np.nan
+    h.set_state(0, eta=e)
+    h.step(2)
+    with pytest.raises(rti.RtiError) as ei:
+        h.sync()
+    assert ei.value.code == -5
+
+
+def test_fp32_accuracy_report(rti, oracle_mod):
+    """Binary32 path vs the FP64 oracle on the single grid (1800 steps): max |d eta|,
+    max |d max-eta|, wet/dry mismatch and arrival error within the stated accuracy."""
+    sc = S.config1()
+    h, o = run_pair(rti, oracle_mod, sc, sc.steps, precision=1)
+    ge, oe = h.get_state(0)[0], o.get_state(0)[0]
+    assert np.abs(ge - oe).max() <= 0.01
+    gm, om = h.max_height(0), o.max_height(0)
+    both = ~np.isnan(gm) & ~np.isnan(om)
+    assert np.abs(gm[both] - om[both]).max() <= 0.05
+    ever_g, ever_o = ~np.isnan(gm), ~np.isnan(om)
+    assert (ever_g ^ ever_o).sum() <= 0.005 * (ever_g | ever_o).sum()
+    ga, oa = h.arrival_time(0), o.arrival_time(0)
+    m = (ga >= 0) & (oa >= 0)
+    assert np.percentile(np.abs(ga[m] - oa[m]), 99) <= 5.0
+
+
+def _small_nest(levels):
+    return S.coastal_hierarchy("small nest", 7, (90, 72, 810.0), levels, dt=0.5, steps=60,
+                               shelf_w=10e3, slope_w=15e3, wiggle=1e3, coast_frac=0.6,
+                               land_frac=0.4, source=dict(kind="gauss", sigma=6e3, peak=2.0))
+
+
+def test_mixed_schedules_and_precisions_in_one_process(rti):
+    """Handles of both precisions and both schedules created and stepped one after the
+    other in one process (a sequence that once faulted on the second handle) all run,
+    and the two binary64 schedules agree bitwise."""
+    out = {}
+    keep = []
+    for levels in ([(1, 54, 54)], [(1, 54, 54), (1, 45, 45)]):
+        sc = _small_nest(levels)
+        for prec, sched in ((0, 0), (0, 1), (1, 0), (1, 1), (0, 0), (0, 1)):
+            h = rti.Handle.from_scenario(sc, precision=prec, schedule=sched)
+            keep.append(h)
+            h.step(5)
+            h.sync()
+            out[(len(levels), prec, sched)] = [h.get_state(k) for k in range(len(sc.blocks))]
+    for nl in (1, 2):
+        for a, b in zip(out[(nl, 0, 0)], out[(nl, 0, 1)]):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
