@@ -885,14 +885,15 @@ static int get_out(rti_handle* h, int block, double* out, int kind) {
   std::vector<double> em(n);
   rc = download(h, m.emax, d.nx, d.ny, m.pitch, true, em.data(), &h->err);
   if (rc) return rc;
+  // the never-wet marker is kNeverWet rounded to the state precision: test by range
   if (kind == 1) {  // max height
-    for (size_t c = 0; c < n; ++c) out[c] = em[c] == kNeverWet ? NAN : em[c];
+    for (size_t c = 0; c < n; ++c) out[c] = em[c] < 0.5 * kNeverWet ? NAN : em[c];
     return RTI_OK;
   }
   std::vector<double> hd(n);
   rc = download(h, m.h, d.nx, d.ny, m.pitch, true, hd.data(), &h->err);
   if (rc) return rc;
-  for (size_t c = 0; c < n; ++c) out[c] = em[c] == kNeverWet ? 0.0 : hd[c] + em[c];
+  for (size_t c = 0; c < n; ++c) out[c] = em[c] < 0.5 * kNeverWet ? 0.0 : hd[c] + em[c];
   return RTI_OK;
 }
 

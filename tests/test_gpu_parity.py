@@ -195,3 +195,19 @@ def test_mixed_schedules_and_precisions_in_one_process(rti):
         for a, b in zip(out[(nl, 0, 0)], out[(nl, 0, 1)]):
             for x, y in zip(a, b):
                 assert np.array_equal(x, y)
+
+
+def test_never_wet_cells_report_nan_height_in_both_precisions(rti, oracle_mod):
+    """Cells that were never wet report max height NaN and max depth 0, whatever the
+    state precision (the binary32 never-wet marker is a rounded -1e30)."""
+    sc = S.config1(nx=64, ny=40, steps=20)
+    sc.bathy[0][:, -12:] = -5.0  # a strip of dry land the wave cannot reach
+    o = oracle_mod.from_scenario(sc)
+    o.step(sc.steps)
+    never = np.isnan(o.max_height(0))
+    assert never.sum() >= 12 * 40
+    for prec in (0, 1):
+        h = rti.Handle.from_scenario(sc, precision=prec)
+        h.step(sc.steps)
+        assert np.array_equal(np.isnan(h.max_height(0)), never)
+        assert np.all(h.max_depth(0)[never] == 0.0)
