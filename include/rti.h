@@ -130,8 +130,55 @@ int rti_num_blocks(const rti_handle* h);
 long long rti_num_cells(const rti_handle* h);
 
 void rti_destroy(rti_handle* h);
+/* message of the handle's last failure; with NULL, of the last failed rti_create or
+ * rti_step_noalloc on the calling thread */
 const char* rti_last_error(const rti_handle* h);
 const char* rti_error_string(int code);
+
+/* ---- Allocation-free stepping of one grid ----
+ * The paper has no counterpart to this call. It serves callers that cannot call
+ * cudaMalloc: a process whose device memory is handed in full to its own pool allocator
+ * (a forecast service that reserves HBM for its scenario slots at start-up), and code
+ * that must not allocate because an allocation can fail once that reservation is made
+ * or can synchronise the device and stall the other streams of a real-time service.
+ * rti_create allocates its arena, tables and events; this call allocates nothing: the
+ * caller owns the state arrays and the call takes its scratch (block descriptor, tile
+ * list, counters, device barrier, status words, budget partials) from one file-scope
+ * device array of about 200 KB that every GPU which loads the library holds until the
+ * process exits. Limit: a single root grid (parent -1) of at most 4096 tiles (2048 x 2048
+ * cells with the default 64 x 16 tiles); larger grids return RTI_ERR_INVALID_ARG and
+ * rti_last_error(NULL) says why.
+ *
+ * State layout (element type double for RTI_FP64, float for RTI_FP32; manning is always
+ * float and arrival_step int): every array has `pitch` elements per row with
+ * pitch >= nx + 9, and ny + 5 rows; element (column c, row r) lives at
+ * (r + 2) * pitch + (c + 4). Cells use columns 0..nx-1 and rows 0..ny-1, M uses columns
+ * 0..nx, N rows 0..ny. eta/M/N come in two time levels: level (steps_done & 1) is the
+ * current one on entry, level ((steps_done + nsteps) & 1) on return. max_eta starts at
+ * eta0 on wet cells and -1e30 elsewhere; arrival_step at 0 where eta0 >= arrival_thr on
+ * wet cells and -1 elsewhere. steps_done numbers the steps for the arrival record.
+ *
+ * The call steps nsteps times on `stream` (a cudaStream_t, NULL = legacy default), waits
+ * for the work and returns its device status (RTI_ERR_NONFINITE, RTI_ERR_TIMEOUT). Its
+ * first call on a device looks up the scratch address; make that first call before any
+ * stream capture. Every call shares the one scratch array, which keeps the previous
+ * call's contents (the call clears what must start at zero); calls that overlap on the
+ * GPU, from several threads or streams, race on it. It does not check Eq. 4 (it reads no
+ * bathymetry on the host). */
+typedef struct {
+  void* eta[2];
+  void* M[2];
+  void* N[2];
+  const void* h;
+  const float* manning;
+  void* max_eta;
+  int* arrival_step;
+  int pitch; /* elements per row of every array */
+} rti_noalloc_state;
+
+int rti_step_noalloc(const rti_block* grid, const rti_params* params,
+                     const rti_noalloc_state* state, long long steps_done, int nsteps,
+                     void* stream);
 
 /* ---- Batches: many hierarchies stepped together in one persistent launch ----
  * All handles of a batch share one precision. A handle in a batch is stepped only by

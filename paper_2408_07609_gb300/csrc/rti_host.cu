@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -26,6 +27,9 @@ cudaError_t debug_check_fp32(int* out8);
 cudaError_t debug_check_fp64(int* out8);
 #endif
 }  // namespace rti
+
+// message of the last rti_create or rti_step_noalloc that failed on this thread
+static thread_local std::string t_create_err;
 
 namespace {
 
@@ -632,9 +636,6 @@ const char* rti_error_string(int code) {
   }
 }
 
-// message of the last rti_create that failed on this thread
-static thread_local std::string t_create_err;
-
 const char* rti_last_error(const rti_handle* h) { return h ? h->err.c_str() : t_create_err.c_str(); }
 
 int rti_footprint(const rti_block* blocks, int nblocks, const rti_params* params, size_t* bytes) {
@@ -1053,3 +1054,189 @@ void rti_batch_destroy(rti_batch* b) {
 }
 
 }  // extern "C"
+
+// ===================================================================== allocation-free step
+// rti_step_noalloc: one root grid stepped with the library's kernels, every piece of
+// scratch (block descriptor, tile list, scenario counters, device barrier, status words,
+// per-tile budget partials) taken from one file-scope device array instead of cudaMalloc.
+namespace {
+
+constexpr int kNoAllocMaxTiles = 4096;  // e.g. 2048 x 2048 cells with 64 x 16 tiles
+
+struct NoAllocScratch {
+  Blk<double> blk;  // holds a Blk<float> or a Blk<double>
+  int counts[2];    // tiles, scenarios
+  int status_group;
+  int status_grid;
+  ScenDev scen;
+  Bar bar;
+  int kids[4];
+  Tile tiles[kNoAllocMaxTiles];
+  double budget[4 * kNoAllocMaxTiles];
+};
+
+}  // namespace
+
+// The scratch itself: ~200 KB, resident on every device that loads the library.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256];  // device address of the scratch, per device ordinal
+
+// Writes the tile list, the descriptor and the counters, and clears the barrier, the
+// status words and the budget partials (the array keeps the previous call's contents).
+template <class T>
+__global__ void k_noalloc_setup(NoAllocScratch* s, Blk<T> b, int tx, int ty, int tiles_x,
+                                int tiles_y, long long steps_done, long long nsteps) {
+  const int nt = tiles_x * tiles_y;
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    Tile t;
+    t.blk = 0;
+    t.x0 = (k % tiles_x) * tx;
+    t.y0 = (k / tiles_x) * ty;
+    t.flags = (t.x0 == 0 ? kTfWest : 0) | (t.x0 + tx >= b.nx ? kTfEast : 0) |
+              (t.y0 == 0 ? kTfSouth : 0) | (t.y0 + ty >= b.ny ? kTfNorth : 0);
+    s->tiles[k] = t;
+    for (int q = 0; q < 4; ++q) s->budget[4 * k + q] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    *reinterpret_cast<Blk<T>*>(&s->blk) = b;
+    s->counts[0] = nt;
+    s->counts[1] = 1;
+    s->status_group = 0;
+    s->status_grid = 0;
+    s->scen.base = steps_done;
+    s->scen.remaining = nsteps;
+    s->bar.count = 0;
+    s->bar.gen = 0;
+  }
+}
+
+template <class T>
+int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
+                const rti_noalloc_state* st, long long steps_done, int nsteps, cudaStream_t stream) {
+  const int tx = p->tile_x ? p->tile_x : kDefaultTx, ty = p->tile_y ? p->tile_y : kDefaultTy;
+  const int tiles_x = (g->nx + tx - 1) / tx, tiles_y = (g->ny + ty - 1) / ty;
+  Blk<T> b;
+  std::memset(&b, 0, sizeof(b));
+  for (int q = 0; q < 2; ++q) {
+    b.eta[q] = (T*)st->eta[q];
+    b.M[q] = (T*)st->M[q];
+    b.N[q] = (T*)st->N[q];
+  }
+  b.h = (const T*)st->h;
+  b.man = st->manning;
+  b.emax = (T*)st->max_eta;
+  b.arr = st->arrival_step;
+  b.nx = g->nx;
+  b.ny = g->ny;
+  b.pitch = st->pitch;
+  b.parent = -1;
+  for (int q = 0; q < 4; ++q) b.bc[q] = g->bc[q];
+  b.tiles_x = tiles_x;
+  b.budget = s->budget;
+  b.status = &s->status_grid;
+  b.dtdx = (T)(p->dt / g->dx);
+  b.dt = (T)p->dt;
+  b.g = (T)p->g;
+  b.cfric = (T)(0.5 * p->dt * p->g);
+  b.eps = (T)p->dry_eps;
+  b.thr = (T)p->arrival_thr;
+  b.dx = (T)g->dx;
+  b.q4dt = (T)(4.0 * p->dt);
+  b.dx2 = g->dx * g->dx;
+  b.vol = p->dt * g->dx;
+  b.eps_d = p->dry_eps;
+#ifdef RTI_CHECKED
+  b.lo = nullptr;
+  b.hi = reinterpret_cast<const char*>(~0ull);
+#endif
+  k_noalloc_setup<T><<<1, 256, 0, stream>>>(s, b, tx, ty, tiles_x, tiles_y, steps_done, nsteps);
+  cudaError_t e = cudaGetLastError();
+  int grid = 0;
+  if (e == cudaSuccess) e = persistent_grid<T>(&grid);
+  if (e == cudaSuccess) {
+    KParams<T> kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.blk = reinterpret_cast<const Blk<T>*>(&s->blk);
+    kp.kids = s->kids;
+    kp.tiles = s->tiles;
+    kp.ntiles = &s->counts[0];
+    kp.scen = &s->scen;
+    kp.status = &s->status_group;
+    kp.bar = &s->bar;
+    kp.nsteps = nsteps;
+    kp.tx = tx;
+    kp.ty = ty;
+    kp.spin_cycles = kSpinCycles;
+#ifdef RTI_CHECKED
+    kp.nblk = 1;
+    kp.nkids = 0;
+#endif
+    e = launch_chunk<T>(kp, p->schedule, grid, &s->counts[1], stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  int words[2] = {0, 0};
+  if (e == cudaSuccess)
+    e = cudaMemcpy(words, &s->status_group, sizeof(words), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    t_create_err = std::string("rti_step_noalloc: ") + cudaGetErrorString(e);
+    return RTI_ERR_CUDA;
+  }
+  if ((words[0] | words[1]) & kStTimeout) return RTI_ERR_TIMEOUT;
+  if (words[1] & kStNonFinite) return RTI_ERR_NONFINITE;
+  return RTI_OK;
+}
+
+}  // namespace
+
+extern "C" int rti_step_noalloc(const rti_block* grid, const rti_params* params,
+                                const rti_noalloc_state* state, long long steps_done, int nsteps,
+                                void* stream) {
+  t_create_err.clear();
+  std::string why;
+  if (!grid || !params || !state || steps_done < 0 || nsteps < 0) return RTI_ERR_INVALID_ARG;
+  int rc = validate(grid, 1, params, &why);
+  if (rc) {
+    t_create_err = "rti_step_noalloc: " + why;
+    return rc;
+  }
+  const int tx = params->tile_x ? params->tile_x : kDefaultTx;
+  const int ty = params->tile_y ? params->tile_y : kDefaultTy;
+  const long long tiles = (long long)((grid->nx + tx - 1) / tx) * ((grid->ny + ty - 1) / ty);
+  if (tiles > kNoAllocMaxTiles) {
+    t_create_err = "rti_step_noalloc: grid of " + std::to_string(tiles) + " tiles exceeds the " +
+                    std::to_string(kNoAllocMaxTiles) + "-tile scratch";
+    return RTI_ERR_INVALID_ARG;
+  }
+  for (int q = 0; q < 2; ++q)
+    if (!state->eta[q] || !state->M[q] || !state->N[q]) return RTI_ERR_INVALID_ARG;
+  if (!state->h || !state->manning || !state->max_eta || !state->arrival_step ||
+      state->pitch < grid->nx + 9) {
+    t_create_err = "rti_step_noalloc: null state array or pitch below nx + 9";
+    return RTI_ERR_INVALID_ARG;
+  }
+  if (nsteps == 0) return RTI_OK;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) return RTI_ERR_CUDA;
+  void* addr = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {  // once per device, with that device current
+      e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        t_create_err = std::string("rti_step_noalloc: scratch address: ") + cudaGetErrorString(e);
+        return RTI_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = addr;
+    }
+    addr = g_noalloc_addr[dev];
+  }
+  NoAllocScratch* s = static_cast<NoAllocScratch*>(addr);
+  cudaStream_t st = (cudaStream_t)stream;
+  return params->precision == RTI_FP32 ? noalloc_run<float>(s, grid, params, state, steps_done, nsteps, st)
+                                       : noalloc_run<double>(s, grid, params, state, steps_done, nsteps, st);
+}

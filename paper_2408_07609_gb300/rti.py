@@ -39,6 +39,13 @@ class Params(C.Structure):
                 ("tile_x", C.c_int), ("tile_y", C.c_int)]
 
 
+class NoAllocState(C.Structure):
+    """Device pointers of a caller-owned single-grid state (rti_noalloc_state)."""
+    _fields_ = [("eta", C.c_void_p * 2), ("M", C.c_void_p * 2), ("N", C.c_void_p * 2),
+                ("h", C.c_void_p), ("manning", C.c_void_p), ("max_eta", C.c_void_p),
+                ("arrival_step", C.c_void_p), ("pitch", C.c_int)]
+
+
 _lib = None
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
@@ -83,6 +90,8 @@ def lib():
             "rti_batch_remaining": (C.c_longlong, [_vp, _vp]),
             "rti_batch_sync": (C.c_int, [_vp]),
             "rti_batch_destroy": (None, [_vp]),
+            "rti_step_noalloc": (C.c_int, [C.POINTER(Block), C.POINTER(Params),
+                                           C.POINTER(NoAllocState), C.c_longlong, C.c_int, _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -289,3 +298,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def noalloc_pitch(nx):
+    """Row pitch (elements) of the library's layout for a grid nx cells wide."""
+    return (nx + 9 + 31) // 32 * 32
+
+
+def step_noalloc(block, params: Params, state: NoAllocState, steps_done, nsteps, stream=None):
+    """rti_step_noalloc: step one caller-owned root grid without any device allocation."""
+    arr = _blocks_array([block])
+    rc = lib().rti_step_noalloc(arr, C.byref(params), C.byref(state), int(steps_done),
+                                int(nsteps), _stream_ptr(stream))
+    if rc:
+        raise RtiError(rc, "rti_step_noalloc: " + (lib().rti_last_error(None) or b"").decode())
