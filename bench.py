@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--tile", type=int, nargs=2, default=(0, 0), help="tile shape (0 0 = default)")
     return ap.parse_args()
 
 
@@ -158,11 +159,11 @@ def workload():
     return scenarios.config4(steps=SIX_HOURS_STEPS)
 
 
-def time_device(rti, sc, precision, steps, warmup, schedule, world):
+def time_device(rti, sc, precision, steps, warmup, schedule, world, tile=(0, 0)):
     """Kernel-only rate: inputs resident in HBM, CUDA events on the launching stream."""
     import torch
 
-    h = rti.Handle.from_scenario(sc, precision=precision, schedule=schedule)
+    h = rti.Handle.from_scenario(sc, precision=precision, schedule=schedule, tile=tuple(tile))
     stream = torch.cuda.Stream()
     h.step(warmup, stream)
     h.sync()
@@ -226,10 +227,11 @@ def run_ours(a):
     sc = workload()
     cells = sc.cells
     with Clocks(local) as clk:
-        ms32 = time_device(rti, sc, rti.FP32, a.steps, a.warmup, a.schedule, world)
+        ms32 = time_device(rti, sc, rti.FP32, a.steps, a.warmup, a.schedule, world, a.tile)
     clocks = clk.summary()
     ms32 = max_over_ranks(ms32, world)
-    ms64 = time_device(rti, sc, rti.FP64, a.fp64_steps, max(3, a.warmup // 2), a.schedule, world)
+    ms64 = time_device(rti, sc, rti.FP64, a.fp64_steps, max(3, a.warmup // 2), a.schedule, world,
+                       a.tile)
     ms64 = max_over_ranks(ms64, world)
     per32, per64 = ms32 / a.steps, ms64 / a.fp64_steps
     gcups32 = world * cells * a.steps / (ms32 / 1e3) / 1e9
@@ -262,6 +264,7 @@ def run_ours(a):
             "config": {"workload": sc.name, "cells": cells, "blocks": len(sc.blocks),
                        "levels": 5, "dt_s": sc.dt, "precision": "fp32",
                        "schedule": "persistent" if a.schedule == 0 else "two launches/step",
+                       "tile": list(a.tile) if a.tile[0] else [64, 16],
                        "l2": "working set 1.9 GB (fp32) > 129 MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "fp64": {"value": gcups64, "unit": "GCUPS", "ms_per_step": per64,

@@ -303,7 +303,8 @@ int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, std::st
     if (c > 0) g->spin_cycles = c;
   }
   if (e == cudaSuccess) {
-    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid) : persistent_grid<double>(&g->grid);
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid, tx, ty)
+                         : persistent_grid<double>(&g->grid, tx, ty);
   }
   if (e != cudaSuccess) return cuda_err(err, e, "group setup");
   return RTI_OK;
@@ -1156,7 +1157,7 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
   k_noalloc_setup<T><<<1, 256, 0, stream>>>(s, b, tx, ty, tiles_x, tiles_y, steps_done, nsteps);
   cudaError_t e = cudaGetLastError();
   int grid = 0;
-  if (e == cudaSuccess) e = persistent_grid<T>(&grid);
+  if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty);
   if (e == cudaSuccess) {
     KParams<T> kp;
     std::memset(&kp, 0, sizeof(kp));

@@ -4,13 +4,29 @@
 
 namespace rti {
 
+// Dynamic shared memory of the copy pipeline; raises the kernels' limit when needed.
+static cudaError_t prepare_smem(int tx, int ty, size_t* bytes) {
+  *bytes = pipe_layout<RTI_T>(tx, ty).total;
+  cudaError_t e = cudaFuncSetAttribute(k_persistent<RTI_T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pass_a<RTI_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)*bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pass_b<RTI_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)*bytes);
+  return e;
+}
+
 template <>
-cudaError_t persistent_grid<RTI_T>(int* grid) {
+cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty) {
   int dev = 0, sms = 0, per = 0;
+  size_t smem = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = prepare_smem(tx, ty, &smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<RTI_T>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<RTI_T>, 256, smem);
   if (e == cudaSuccess) *grid = sms * (per > 0 ? per : 1);
   return e;
 }
@@ -18,7 +34,9 @@ cudaError_t persistent_grid<RTI_T>(int* grid) {
 template <>
 cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid,
                                 const int* nscen, cudaStream_t st) {
-  cudaError_t e = cudaSuccess;
+  size_t smem = 0;
+  cudaError_t e = prepare_smem(kp.tx, kp.ty, &smem);
+  if (e != cudaSuccess) return e;
   const dim3 blk(32, 8);
   if (schedule == 0) {
     e = cudaMemsetAsync(kp.bar, 0, sizeof(Bar), st);
@@ -26,7 +44,7 @@ cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = blk;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -36,10 +54,10 @@ cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid
     e = cudaLaunchKernelEx(&cfg, k_persistent<RTI_T>, kp);
   } else {
     for (int s = 0; s < kp.nsteps && e == cudaSuccess; ++s) {
-      k_pass_a<RTI_T><<<grid, blk, 0, st>>>(kp, s);
+      k_pass_a<RTI_T><<<grid, blk, smem, st>>>(kp, s);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
-      k_pass_b<RTI_T><<<grid, blk, 0, st>>>(kp, s);
+      k_pass_b<RTI_T><<<grid, blk, smem, st>>>(kp, s);
       e = cudaGetLastError();
     }
   }

@@ -20,6 +20,6 @@ template <class T>
 cudaError_t launch_fill_edges(const KParams<T>& kp, int grid, int parity, cudaStream_t st);
 // largest co-resident grid of the persistent kernel on the current device
 template <class T>
-cudaError_t persistent_grid(int* grid);
+cudaError_t persistent_grid(int* grid, int tx, int ty);
 
 }  // namespace rti
