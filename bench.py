@@ -30,11 +30,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SIX_HOURS_STEPS = 108_000  # 6 h at dt = 0.2 s (Sec. V-A)
-# compulsory HBM bytes per cell-step of the two-pass step. Pass A reads eta, M, N, h and
-# max-eta and writes eta; pass B reads eta, h, M, N and Manning n (binary32 in both
-# precisions) and writes M and N.
-BYTES_PER_CELL_STEP = {"f32": (5 * 4 + 4) + (5 * 4 + 2 * 4),      # 24 + 28 = 52
-                       "f64": (5 * 8 + 8) + (4 * 8 + 4 + 2 * 8)}  # 48 + 52 = 100
+# Compulsory HBM bytes per cell and step of the one-sweep kernel: it reads eta^n, M^n,
+# N^n, h, eta_max (state precision) and Manning n (binary32) and writes eta^{n+1},
+# M^{n+1}, N^{n+1}; the rare eta_max / arrival writes are not counted.
+BYTES_PER_CELL_STEP = {"f32": 5 * 4 + 4 + 3 * 4,   # 36
+                       "f64": 5 * 8 + 4 + 3 * 8}   # 68
 
 
 def parse():
@@ -278,7 +278,7 @@ def run_ours(a):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_kind": f"{kind} hbm_gbs",
-                         "bytes_per_cell_step": bpc, "kernel": "k_persistent<float>"},
+                         "bytes_per_cell_step": bpc, "kernel": "k_step<float>"},
             "cpu_baseline": cpu,
             "clocks": clocks,
         })

@@ -49,7 +49,7 @@ extern "C" {
                       the volume budget and the nesting sums accumulate in binary64 */
 
 #define RTI_SCHED_PERSISTENT 0 /* one cooperative launch per chunk of steps, device-wide barriers */
-#define RTI_SCHED_PER_PASS 1   /* two launches per step (mass pass, momentum pass) */
+#define RTI_SCHED_PER_PASS 1   /* one ordinary launch per step (no device-wide barrier) */
 
 /* One rectangular block of a grid level (Sec. II-A "blocks"). */
 typedef struct {
@@ -68,7 +68,9 @@ typedef struct {
   double arrival_thr; /* arrival: max eta first >= this (m; 0.01) */
   int precision;      /* RTI_FP64 or RTI_FP32 */
   int schedule;       /* RTI_SCHED_* */
-  int tile_x, tile_y; /* tile shape in cells, 0 = library default */
+  int tile_x;         /* strip width in cells: 0 or 28 (a warp's 32 lanes less a 2-cell halo
+                         on each side); other values are RTI_ERR_INVALID_ARG */
+  int tile_y;         /* strip height in cells, a multiple of 8; 0 = 32 */
 } rti_params;
 
 typedef struct rti_handle rti_handle;
@@ -145,8 +147,8 @@ const char* rti_error_string(int code);
  * caller owns the state arrays and the call takes its scratch (block descriptor, tile
  * list, counters, device barrier, status words, budget partials) from one file-scope
  * device array of about 200 KB that every GPU which loads the library holds until the
- * process exits. Limit: a single root grid (parent -1) of at most 4096 tiles (2048 x 2048
- * cells with the default 64 x 16 tiles); larger grids return RTI_ERR_INVALID_ARG and
+ * process exits. Limit: a single root grid (parent -1) of at most 4096 strips (2048 x 2048
+ * cells make 4736 of 28 x 32 strips: use tile_y = 64 there); larger grids return RTI_ERR_INVALID_ARG and
  * rti_last_error(NULL) says why.
  *
  * State layout (element type double for RTI_FP64, float for RTI_FP32; manning is always

@@ -33,13 +33,14 @@ static thread_local std::string t_create_err;
 
 namespace {
 
-constexpr int kDefaultTx = 64, kDefaultTy = 16;
+constexpr int kDefaultTx = kStripW, kDefaultTy = 32;
 constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at the maximum SM clock
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct BlkMem {
   size_t eta[2], M[2], N[2], h, emax, man, arr, budget;
+  size_t ring;  // fine-to-coarse overrides of a block with children (0 = none)
   int pitch;
   long long rows;
   int tiles_x, tiles_y;
@@ -70,6 +71,9 @@ size_t plan_layout(const rti_block* b, int nb, int prec, int tx, int ty, std::ve
     m.emax = take(plane * es);
     m.man = take(plane * 4);
     m.arr = take(plane * 4);
+    bool parent_of_some = false;
+    for (int c = 0; c < nb; ++c) parent_of_some |= b[c].parent == k;
+    m.ring = parent_of_some ? take(plane * es) : 0;
     m.tiles_x = (b[k].nx + tx - 1) / tx;
     m.tiles_y = (b[k].ny + ty - 1) / ty;
     m.budget = take((size_t)m.tiles_x * m.tiles_y * 4 * sizeof(double));
@@ -89,7 +93,7 @@ int validate(const rti_block* bl, int nb, const rti_params* p, std::string* why)
   if (!(p->dt > 0) || !(p->g > 0) || !(p->dry_eps >= 0) ||
       (p->precision != RTI_FP32 && p->precision != RTI_FP64) ||
       (p->schedule != RTI_SCHED_PERSISTENT && p->schedule != RTI_SCHED_PER_PASS) ||
-      p->tile_x < 0 || p->tile_y < 0 || p->tile_x % 32 || p->tile_y % 8) {
+      (p->tile_x != 0 && p->tile_x != kStripW) || p->tile_y < 0 || p->tile_y % 8) {
     *why = "bad params (dt, g, dry_eps, precision, schedule or tile shape)";
     return RTI_ERR_INVALID_ARG;
   }
@@ -225,6 +229,7 @@ Blk<T> make_blk(rti_handle* h, int k, int base_index, int scen, int child_first,
   b.man = (const float*)(A + m.man);
   b.emax = (T*)(A + m.emax);
   b.arr = (int*)(A + m.arr);
+  b.ring = m.ring ? (T*)(A + m.ring) : nullptr;
   b.nx = d.nx;
   b.ny = d.ny;
   b.pitch = m.pitch;
@@ -379,12 +384,14 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
           if (t.x0 + g->tx >= d.nx) t.flags |= kTfEast;
           if (t.y0 == 0) t.flags |= kTfSouth;
           if (t.y0 + g->ty >= d.ny) t.flags |= kTfNorth;
-          for (int c : ch[k]) {  // tile meets the inner ring of a child footprint
+          // the strip recomputes eta^{n+1} on a 2-cell halo: flag it when that halo
+          // meets the inner ring of a child footprint
+          const int hx0 = t.x0 - 2, hy0 = t.y0 - 2, hx1 = t.x0 + g->tx + 2, hy1 = t.y0 + g->ty + 2;
+          for (int c : ch[k]) {
             const rti_block& cd = h->blocks[c];
             int a0 = cd.i0, a1 = cd.i0 + cd.nx / 3, b0 = cd.j0, b1 = cd.j0 + cd.ny / 3;
-            int x1 = t.x0 + g->tx, y1 = t.y0 + g->ty;
-            bool meets = t.x0 < a1 && a0 < x1 && t.y0 < b1 && b0 < y1;
-            bool inner = t.x0 >= a0 + 1 && x1 <= a1 - 1 && t.y0 >= b0 + 1 && y1 <= b1 - 1;
+            bool meets = hx0 < a1 && a0 < hx1 && hy0 < b1 && b0 < hy1;
+            bool inner = hx0 >= a0 + 1 && hx1 <= a1 - 1 && hy0 >= b0 + 1 && hy1 <= b1 - 1;
             if (meets && !inner) t.flags |= kTfRing;
           }
           tiles.push_back(t);
@@ -704,6 +711,10 @@ int rti_create(const rti_block* blocks, int nblocks, const double* const* bathy,
     return code;
   };
   e = cudaMemset(h->arena, 0, h->arena_bytes);
+  for (int k = 0; k < nblocks && e == cudaSuccess; ++k) {  // ring overrides start unset
+    const BlkMem& m = h->mem[k];
+    if (m.ring) e = cudaMemset(h->arena + m.ring, 0xFF, (size_t)m.pitch * m.rows * esize(h->prec));
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cuda_err(&h->err, e, "arena setup");
@@ -1062,7 +1073,7 @@ void rti_batch_destroy(rti_batch* b) {
 // per-tile budget partials) taken from one file-scope device array instead of cudaMalloc.
 namespace {
 
-constexpr int kNoAllocMaxTiles = 4096;  // e.g. 2048 x 2048 cells with 64 x 16 tiles
+constexpr int kNoAllocMaxTiles = 4096;  // e.g. 2048 x 2048 cells in 28 x 64 strips (2368)
 
 struct NoAllocScratch {
   Blk<double> blk;  // holds a Blk<float> or a Blk<double>
@@ -1223,6 +1234,20 @@ extern "C" int rti_step_noalloc(const rti_block* grid, const rti_params* params,
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 256) return RTI_ERR_CUDA;
+  {  // every array must be memory the device can address (no launch on a stray pointer)
+    const void* arr[10] = {state->eta[0], state->eta[1], state->M[0],       state->M[1],
+                           state->N[0],   state->N[1],   state->h,          state->manning,
+                           state->max_eta, state->arrival_step};
+    for (const void* a : arr) {
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, a) != cudaSuccess || at.devicePointer == nullptr ||
+          (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        t_create_err = "rti_step_noalloc: a state array is not device memory";
+        return RTI_ERR_INVALID_ARG;
+      }
+    }
+  }
   void* addr = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);

@@ -4,29 +4,14 @@
 
 namespace rti {
 
-// Dynamic shared memory of the copy pipeline; raises the kernels' limit when needed.
-static cudaError_t prepare_smem(int tx, int ty, size_t* bytes) {
-  *bytes = pipe_layout<RTI_T>(tx, ty).total;
-  cudaError_t e = cudaFuncSetAttribute(k_persistent<RTI_T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pass_a<RTI_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)*bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pass_b<RTI_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)*bytes);
-  return e;
-}
-
 template <>
 cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty) {
+  (void)tx;
+  (void)ty;
   int dev = 0, sms = 0, per = 0;
-  size_t smem = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = prepare_smem(tx, ty, &smem);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<RTI_T>, 256, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T>, 256, 0);
   if (e == cudaSuccess) *grid = sms * (per > 0 ? per : 1);
   return e;
 }
@@ -34,30 +19,25 @@ cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty) {
 template <>
 cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid,
                                 const int* nscen, cudaStream_t st) {
-  size_t smem = 0;
-  cudaError_t e = prepare_smem(kp.tx, kp.ty, &smem);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   const dim3 blk(32, 8);
-  if (schedule == 0) {
+  if (schedule == 0) {  // one cooperative launch for the whole chunk
     e = cudaMemsetAsync(kp.bar, 0, sizeof(Bar), st);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = blk;
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_persistent<RTI_T>, kp);
-  } else {
+    e = cudaLaunchKernelEx(&cfg, k_step<RTI_T>, kp, 0, kp.nsteps);
+  } else {  // one launch per step
     for (int s = 0; s < kp.nsteps && e == cudaSuccess; ++s) {
-      k_pass_a<RTI_T><<<grid, blk, smem, st>>>(kp, s);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      k_pass_b<RTI_T><<<grid, blk, smem, st>>>(kp, s);
+      k_step<RTI_T><<<grid, blk, 0, st>>>(kp, s, 1);
       e = cudaGetLastError();
     }
   }

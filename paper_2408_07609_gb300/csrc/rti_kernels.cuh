@@ -1,31 +1,30 @@
 // rti_kernels.cuh -- sm_103a kernels of the nested TUNAMI-N2 leap-frog step.
 //
 // Included by rti_fp32.cu and rti_fp64.cu, which instantiate it for binary32 and
-// binary64 state. One time step is two passes over a tile work list that holds the
-// tiles of every block of every scenario in a batch:
+// binary64 state. One time step is one sweep over a work list of strips (28 columns x
+// ty rows of one block) that covers every block of every scenario in a batch. A warp
+// steps a strip by marching up its rows and, at each row, computes
 //
-//   pass A (Eq. 1, Sec. IV-A "NLMASS"): eta^{n+1} = eta^n - dt/dx (dM + dN), the dry
-//     clip, the coarse-to-fine edge fluxes of a child (pulled from the parent's
-//     current fluxes and stored into the child's flux array), the fine-to-coarse
-//     ring of a parent (Listing 5 mean of the 3x3 child cells, recomputed from the
-//     child's stable time level), max height / arrival (output update) and the
-//     per-tile binary64 volume budget (warp-shuffle reduction);
-//   pass B (Eqs. 2-3, "NLMNT2"/XMMT/YMMT): M^{n+1}, N^{n+1} with upwind advection,
-//     pressure on the total depth, semi-implicit Manning friction, the wet/dry front
-//     and the outflow limit; radiation or wall faces on root edges. A tile stages its
-//     fields with a two-cell halo in shared memory, computes every face's advective
-//     fluxes once, then updates its faces from shared memory.
+//   the mass update (Eq. 1, Sec. IV-A "NLMASS"): eta^{n+1} = eta^n - dt/dx (dM + dN),
+//     the dry clip, the coarse-to-fine edge fluxes of a child (pulled from the
+//     parent's current fluxes), the fine-to-coarse ring of a parent (Listing 5 mean of
+//     the 3x3 child cells, recomputed from the child's stable time level), max height
+//     and arrival (output update) and the binary64 volume budget (warp-shuffle sums);
+//   the momentum update of the row below (Eqs. 2-3, "NLMNT2"/XMMT/YMMT): M^{n+1},
+//     N^{n+1} with upwind advection, pressure on the total depth, semi-implicit
+//     Manning friction, the wet/dry front and the outflow limit; radiation or wall
+//     faces on root edges.
 //
-// eta, M and N are ping-ponged (parity = step & 1), so no pass reads what it writes
-// and every pull reads a time level that no tile of the same pass modifies.
+// eta, M and N are ping-ponged (parity = step & 1): a step reads level p and writes
+// level p ^ 1, and every pull reads a level that no strip of the step modifies.
 // The discrete rules follow the oracle's readings R1-R10 operation for operation;
 // the binary64 build uses -fmad=false so that it rounds like the oracle.
 //
-// Block descriptors: a tile copies its block's descriptor (and, for a child, its
-// parent's) into shared memory once and reads fields from there. Optimised binary64
-// builds that re-read descriptor fields through references into the device table
-// faulted on an in-range edge read (the range-checked, -G and copied-descriptor builds
-// did not); the mixed-sequence GPU test guards this.
+// Block descriptors: a warp copies its strip's block descriptor (and, for a child, its
+// parent's) into shared memory and reads fields from there. Optimised binary64 builds
+// of an earlier kernel that re-read descriptor fields through references into the
+// device table faulted on an in-range edge read (the range-checked, -G and
+// copied-descriptor builds did not); the mixed-sequence GPU test guards this.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -155,17 +154,18 @@ __device__ T child_eta_next(const Blk<T>& c, const Blk<T>& P, int p, int x, int 
 }
 
 // ------------------------------------------------------------------ fine -> coarse (R8)
-// If parent cell (I, J) of block b lies on the inner ring of a child footprint and the
-// 3x3 patch has a wet cell, store the floored mean of the wet child levels in `out`.
+// Parent cell (I, J) of block b: 0 if it is not on the inner ring of a child footprint,
+// 1 if it is but the 3x3 child patch has no wet cell, 2 if `out` holds the floored mean
+// of the patch's wet child levels at eta^{n+1} (recomputed from the child's level p).
 template <class T>
-__device__ __noinline__ bool ring_value(const KParams<T>& kp, const Blk<T>& b, int p, int I,
-                                        int J, T hP, T& out) {
+__device__ __noinline__ int ring_value(const KParams<T>& kp, const Blk<T>& b, int p, int I, int J,
+                                       T hP, T& out) {
   for (int q = 0; q < b.child_count; ++q) {
     const Blk<T> c = RTI_BLK(kp, RTI_KID(kp, b.child_first + q));
     int a = c.nx / 3, bb = c.ny / 3;
     int u = I - c.i0, v = J - c.j0;
     if (u < 0 || v < 0 || u >= a || v >= bb) continue;
-    if (!(u == 0 || u == a - 1 || v == 0 || v == bb - 1)) return false;
+    if (!(u == 0 || u == a - 1 || v == 0 || v == bb - 1)) return 0;
     double sum = 0.0;
     int wet = 0;
     for (int x = 3 * u; x < 3 * u + 3; ++x) {    // outer: x (the paper's J)
@@ -177,14 +177,23 @@ __device__ __noinline__ bool ring_value(const KParams<T>& kp, const Blk<T>& b, i
         }
       }
     }
-    if (wet == 0) return false;
+    if (wet == 0) return 1;
     double avg = sum * (1.0 / (double)wet);
     if (avg < -(double)hP) avg = -(double)hP;
     out = (T)avg;
-    return true;
+    return 2;
   }
-  return false;
+  return 0;
 }
+
+// "no override" in a ring plane: all-ones bits (a NaN that arithmetic never produces
+// from finite data and that the kernels test by its bits)
+__device__ __forceinline__ bool ring_unset(float v) { return __float_as_uint(v) == 0xffffffffu; }
+__device__ __forceinline__ bool ring_unset(double v) {
+  return __double_as_longlong(v) == (long long)-1;
+}
+__device__ __forceinline__ float ring_none(float) { return __uint_as_float(0xffffffffu); }
+__device__ __forceinline__ double ring_none(double) { return __longlong_as_double(-1LL); }
 
 // ------------------------------------------------------------------ momentum (R2-R4, R6)
 template <class T>
@@ -241,62 +250,88 @@ __device__ __forceinline__ T limit_outflow(T m, T Dlo, T Dhi, T dx, T q4dt) {
   return m;
 }
 
-// Shared-memory tile of pass B. Local point (lx, ly) holds cell, x-face and y-face
-// (x0 - 2 + lx, y0 - 2 + ly) of the block; W = tx + 4 columns, ty + 4 rows.
-//   E, H, NM, MX, NY : eta^{n+1}, h, Manning n, M^n, N^n (loaded, zero off the margins)
-//   QX, RX, VX       : M^2/D, M Nbar/D and "usable by advection" of x-faces
-//   SY, TY, VY       : N^2/D, N Mbar/D and "usable by advection" of y-faces
+// ------------------------------------------------------------------ block reduction
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ the fused step
+// A step is one sweep over strips. A strip is kStripW columns x ty rows of one block
+// and is stepped by one warp: lane L holds column c = x0 - 2 + L; lanes 2..29 own the
+// strip's cells and faces, lanes 0, 1, 30 and 31 recompute the halo that the stencils
+// read. The warp marches up the rows. At row r it loads eta^n, h, M^n, N^n (of the face
+// above), eta_max and Manning n; forms eta^{n+1} of row r (Eq. 1 with the dry clip,
+// the pulled child-edge fluxes and the ring mean), stores it with the output update of
+// the owned cells, and forms the advective face terms of row r. It then updates the
+// fluxes of row r - 1 (Eqs. 2-3), whose stencil -- eta^{n+1} and face terms of rows
+// r-2..r, columns c-1..c+1 -- is complete in its registers and its neighbours'.
+// The two passes of the paper's step (mass, then momentum) thus become one sweep in
+// which eta^{n+1} is recomputed on the halo instead of being stored and re-read; the
+// arithmetic of every value is the same expression in the same order.
+
+// One row of a lane's column as the march carries it (record of row r, cell (c, r),
+// x-face (c, r) between cells c-1 and c, y-face (c, r) between rows r-1 and r).
 template <class T>
-struct BTile {
-  T *E, *H, *MX, *NY, *QX, *RX, *SY, *TY;
-  float* NM;
-  unsigned char *VX, *VY;
-  int W;
+struct Row {
+  T E, H;        // eta^{n+1}, h of cell (c, r)
+  T eL, hL;      // the same of cell (c - 1, r)
+  T MX, mE;      // M^n of x-faces (c, r) and (c + 1, r)
+  T NY;          // N^n of y-face (c, r)
+  T nb;          // N-bar of x-face (c, r)
+  T QX, RX;      // M^2/D and M N-bar/D of x-face (c, r)
+  T mb;          // M-bar of y-face (c, r)
+  T SY, TY;      // N^2/D and N M-bar/D of y-face (c, r)
+  float nm;      // Manning n of cell (c, r)
+  bool vx, vy;   // x-/y-face (c, r) is interior with D > dry_eps (usable by advection)
 };
 
-__host__ __device__ __forceinline__ size_t btile_bytes(int tx, int ty, size_t elem) {
-  const size_t P = (size_t)(tx + 4) * (size_t)(ty + 4);
-  return (P * (8 * elem + 4 + 2) + 15) / 16 * 16;
-}
+// Raw inputs of row r: eta^n, h, M^n, eta_max, Manning n of (c, r); N^n of y-face (c, r+1).
+template <class T>
+struct Raw {
+  T e, h, m, nn, em;
+  float nm;
+};
 
 template <class T>
-__device__ __forceinline__ BTile<T> carve_btile(unsigned char* base, int tx, int ty) {
-  BTile<T> S;
-  S.W = tx + 4;
-  const int P = (tx + 4) * (ty + 4);
-  T* t = reinterpret_cast<T*>(base);
-  S.E = t;
-  S.H = t + P;
-  S.MX = t + 2 * P;
-  S.NY = t + 3 * P;
-  S.QX = t + 4 * P;
-  S.RX = t + 5 * P;
-  S.SY = t + 6 * P;
-  S.TY = t + 7 * P;
-  S.NM = reinterpret_cast<float*>(t + 8 * P);
-  S.VX = reinterpret_cast<unsigned char*>(S.NM + P);
-  S.VY = S.VX + P;
-  return S;
+__device__ __forceinline__ Raw<T> load_raw(const T* eta, const T* h, const T* M, const T* N,
+                                           const T* emax, const float* man, size_t o,
+                                           int pitch, bool ok) {
+  Raw<T> R;
+  if (ok) {
+    R.e = __ldcg(eta + o);
+    R.h = __ldcg(h + o);
+    R.m = __ldcg(M + o);
+    R.nn = __ldcg(N + o + pitch);
+    R.em = __ldcg(emax + o);
+    R.nm = __ldcg(man + o);
+  } else {
+    R.e = R.h = R.m = R.nn = R.em = T(0);
+    R.nm = 0.0f;
+  }
+  return R;
 }
 
-// R2 + R4 at interior x-face (f, j); k = local index of cell (f, j)
+__device__ __forceinline__ bool lane_bit(unsigned mask, int lane, int d) {
+  return d < 0 ? ((mask << 1) >> lane) & 1u : ((mask >> lane) >> 1) & 1u;
+}
+
+// R2 + R4 at x-face (c, j): cells W = (c-1, j), E = (c, j); QX of faces c-1, c, c+1
+// and RX of rows j-1, j, j+1 with their usable flags.
 template <class T>
-__device__ __forceinline__ T xmom_s(const Blk<T>& b, const BTile<T>& S, int k) {
-  const T eps = b.eps;
-  const int W = S.W;
-  const T eL = S.E[k - 1], eR = S.E[k], hL = S.H[k - 1], hR = S.H[k];
+__device__ __forceinline__ T xmom_r(T hL, T eL, T hR, T eR, T m, T nb, bool okm, T qm, T q0,
+                                    bool okp, T qp, bool oks, T rs, T r0, bool okn, T rn,
+                                    float nL, float nR, T eps, T dtdx, T g, T cfric, T dx,
+                                    T q4dt) {
   const bool wL = hL + eL > eps, wR = hR + eR > eps;
-  const T m = S.MX[k];
-  const T nb = T(0.25) * ((S.NY[k - 1] + S.NY[k]) + (S.NY[k - 1 + W] + S.NY[k + W]));
   T Df, grad, adv;
   if (wL && wR) {
     Df = T(0.5) * (hL + hR) + T(0.5) * (eL + eR);
     grad = eR - eL;
-    const bool okm = S.VX[k - 1], okp = S.VX[k + 1];
-    const T ax = upwind(m, okm ? S.QX[k - 1] : T(0), S.QX[k], okp ? S.QX[k + 1] : T(0), okm, okp);
-    const bool oks = S.VX[k - W], okn = S.VX[k + W];
-    const T ay = upwind(nb, oks ? S.RX[k - W] : T(0), S.RX[k], okn ? S.RX[k + W] : T(0), oks, okn);
-    adv = b.dtdx * (ax + ay);
+    const T ax = upwind(m, okm ? qm : T(0), q0, okp ? qp : T(0), okm, okp);
+    const T ay = upwind(nb, oks ? rs : T(0), r0, okn ? rn : T(0), oks, okn);
+    adv = dtdx * (ax + ay);
   } else if (wL && !wR && eL > -hR) {
     Df = eL + hR;
     grad = -hR - eL;
@@ -309,31 +344,27 @@ __device__ __forceinline__ T xmom_s(const Blk<T>& b, const BTile<T>& S, int k) {
     return T(0);
   }
   if (!(Df > eps)) return T(0);
-  const float nL = S.NM[k - 1], nR = S.NM[k];
   const T nf = (T)(nL > nR ? nL : nR);
-  const T m1 = flux_update(b, m, nb, Df, grad, adv, nf);
+  const T m1 = Ar<T>::update(m, nb, Df, grad, adv, nf, g, dtdx, cfric);
   if (!(wL && wR) && (wL ? m1 < T(0) : m1 > T(0))) return T(0);
-  return limit_outflow(m1, hL + eL, hR + eR, b.dx, b.q4dt);
+  return limit_outflow(m1, hL + eL, hR + eR, dx, q4dt);
 }
 
-// R3 + R4 at interior y-face (i, g); k = local index of cell (i, g)
+// R3 + R4 at y-face (c, j): cells S = (c, j-1), N = (c, j); SY of rows j-1, j, j+1 and
+// TY of faces c-1, c, c+1 with their usable flags.
 template <class T>
-__device__ __forceinline__ T ymom_s(const Blk<T>& b, const BTile<T>& S, int k) {
-  const T eps = b.eps;
-  const int W = S.W;
-  const T eS = S.E[k - W], eN = S.E[k], hS = S.H[k - W], hN = S.H[k];
+__device__ __forceinline__ T ymom_r(T hS, T eS, T hN, T eN, T v, T mb, bool okm, T sm, T s0,
+                                    bool okp, T sp, bool okw, T tw, T t0, bool oke, T te,
+                                    float nS, float nN, T eps, T dtdx, T g, T cfric, T dx,
+                                    T q4dt) {
   const bool wS = hS + eS > eps, wN = hN + eN > eps;
-  const T v = S.NY[k];
-  const T mb = T(0.25) * ((S.MX[k - W] + S.MX[k]) + (S.MX[k - W + 1] + S.MX[k + 1]));
   T Df, grad, adv;
   if (wS && wN) {
     Df = T(0.5) * (hS + hN) + T(0.5) * (eS + eN);
     grad = eN - eS;
-    const bool okm = S.VY[k - W], okp = S.VY[k + W];
-    const T ay = upwind(v, okm ? S.SY[k - W] : T(0), S.SY[k], okp ? S.SY[k + W] : T(0), okm, okp);
-    const bool okw = S.VY[k - 1], oke = S.VY[k + 1];
-    const T ax = upwind(mb, okw ? S.TY[k - 1] : T(0), S.TY[k], oke ? S.TY[k + 1] : T(0), okw, oke);
-    adv = b.dtdx * (ay + ax);
+    const T ay = upwind(v, okm ? sm : T(0), s0, okp ? sp : T(0), okm, okp);
+    const T ax = upwind(mb, okw ? tw : T(0), t0, oke ? te : T(0), okw, oke);
+    adv = dtdx * (ay + ax);
   } else if (wS && !wN && eS > -hN) {
     Df = eS + hN;
     grad = -hN - eS;
@@ -346,133 +377,30 @@ __device__ __forceinline__ T ymom_s(const Blk<T>& b, const BTile<T>& S, int k) {
     return T(0);
   }
   if (!(Df > eps)) return T(0);
-  const float nS = S.NM[k - W], nN = S.NM[k];
   const T nf = (T)(nS > nN ? nS : nN);
-  const T v1 = flux_update(b, v, mb, Df, grad, adv, nf);
+  const T v1 = Ar<T>::update(v, mb, Df, grad, adv, nf, g, dtdx, cfric);
   if (!(wS && wN) && (wS ? v1 < T(0) : v1 > T(0))) return T(0);
-  return limit_outflow(v1, hS + eS, hN + eN, b.dx, b.q4dt);
+  return limit_outflow(v1, hS + eS, hN + eN, dx, q4dt);
 }
 
-// R6: flux leaving through a root edge next to cell k (sign +1 east/north, -1 west/south)
+// R6: flux leaving through a root edge next to a cell (sign +1 east/north, -1 west/south)
 template <class T>
-__device__ __forceinline__ T radiate_s(const Blk<T>& b, const BTile<T>& S, int k, T sign) {
-  const T h = S.H[k], e = S.E[k];
-  if (!(h + e > b.eps)) return T(0);
-  return sign * (dsqrt(b.g * (h > T(0) ? h : T(0))) * e);
+__device__ __forceinline__ T radiate_r(T h, T e, T sign, T eps, T g) {
+  if (!(h + e > eps)) return T(0);
+  return sign * (dsqrt(g * (h > T(0) ? h : T(0))) * e);
 }
 
-// ------------------------------------------------------------------ block reduction
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// ------------------------------------------------------------------ async copy pipeline
-// A CTA walks its tiles of one pass with two shared-memory stages: warp 0 issues the
-// bulk copies (cp.async.bulk, one per row segment of each field) of the next tile into
-// one stage while all warps compute the tile held in the other. Each stage has an
-// mbarrier that completes when the copies have landed (transaction count) and warp 0
-// has arrived; every wait on it is bounded.
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false after `limit` cycles (the caller records a timeout).
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
-                                          long long limit) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > limit) return false;
-  }
-  return true;
-}
-// One bulk copy global -> shared of `bytes` (both 16-byte aligned, bytes % 16 == 0).
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-// Generic-proxy accesses before this point are ordered before later async-proxy ones.
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async;" ::: "memory");
-}
-
-// Shared-memory layout of the pipeline (host and device agree on it).
-struct PipeLayout {
-  int SW, SH;          // stage row width (elements) and rows
-  size_t hdr, stage, derived, total;
-};
+// Per-warp shared memory: the strip's block descriptor (and its parent's), the lanes'
+// binary64 budget partials (clip, outflow, ring) and the block index staged.
 template <class T>
-struct SlotHdr {       // what the issuing warp records for the tile in a stage
-  Blk<T> b;            // the tile's block descriptor
-  Blk<T> P;            // its parent's (children only)
-  Tile td;
-  int p, sn, active;
-};
-// The issuing warp's cache of the last block it staged (tiles of a CTA mostly come
-// from the same block): descriptors and the scenario counters of this chunk.
-template <class T>
-struct IssueCache {
+struct WarpSlot {
   Blk<T> b;
   Blk<T> P;
+  double acc[3][32];
   ScenDev sc;
-  int blk;  // block index of the cached entry, -1 when empty
-};
-template <class T>
-__host__ __device__ __forceinline__ PipeLayout pipe_layout(int tx, int ty) {
-  PipeLayout L;
-  L.SW = tx + 8;
-  L.SH = ty + 4;
-  const size_t n = (size_t)L.SW * L.SH;
-  L.hdr = (2 * sizeof(unsigned long long) + 2 * sizeof(SlotHdr<T>) + sizeof(IssueCache<T>) +
-           127) / 128 * 128;
-  // pass B: eta^{n+1}, h, M, N (T) and Manning n (float); pass A needs less
-  L.stage = (n * (4 * sizeof(T) + sizeof(float)) + 127) / 128 * 128;
-  // pass B's face terms QX, RX, SY, TY (T) and the two validity byte arrays
-  L.derived = (n * (4 * sizeof(T) + 2) + 127) / 128 * 128;
-  L.total = L.hdr + 2 * L.stage + L.derived;
-  return L;
-}
-
-struct PipeState {
-  unsigned phase;  // bit s: parity of stage s's next completion
+  int blk;
 };
 
-// Static shared memory of the step kernels.
-struct StepShared {
-  double red[4][8];
-  int go;
-  int fail;
-};
-
-// Warp 0: record tile t in slot H and issue the copies of the rows pass A (passB false)
-// or pass B (passB true) reads into `stage`, completing on `bar`.
-//   pass A rows y0..ye-1 (N one more), columns [x0, x0 + tx + 4): eta^n, M^n, N^n, h, max
-//   pass B rows y0-2..ye+1, columns [x0 - 4, x0 + tx + 4): eta^{n+1}, h, M^n, N^n, n
-// Column ends are clamped to the allocated row (pitch - 4), row ends to ny + 2; every
-// segment starts on a 16-byte boundary (x0 is a multiple of the 32-wide tile).
 template <class T>
 __device__ __forceinline__ void warp_copy(void* dst, const void* src, int bytes) {
   const unsigned* s = reinterpret_cast<const unsigned*>(src);
@@ -480,298 +408,222 @@ __device__ __forceinline__ void warp_copy(void* dst, const void* src, int bytes)
   for (int w = threadIdx.x; w < bytes / 4; w += 32) d[w] = s[w];
 }
 
+// Stage block `blk`'s descriptor (and its parent's) and scenario counters in the warp's
+// slot, unless they are there already.
 template <class T>
-__device__ void issue_tile(const KParams<T>& kp, int t, int s, bool passB, SlotHdr<T>& H,
-                           IssueCache<T>& cache, unsigned char* stage, unsigned long long* bar,
-                           const PipeLayout& L) {
-  const int lane = threadIdx.x;
-  const Tile td = kp.tiles[t];
-  if (td.blk != cache.blk) {  // new block: descriptors and counters from the device tables
-    warp_copy<T>(&cache.b, &RTI_BLK(kp, td.blk), sizeof(Blk<T>));
-    __syncwarp();
-    if (cache.b.is_child) warp_copy<T>(&cache.P, &RTI_BLK(kp, cache.b.parent), sizeof(Blk<T>));
-    if (lane == 0) {
-      cache.sc = kp.scen[cache.b.scen];
-      cache.blk = td.blk;
-    }
-    __syncwarp();
-  }
-  warp_copy<T>(&H.b, &cache.b, sizeof(Blk<T>));
-  if (cache.b.is_child && !passB) warp_copy<T>(&H.P, &cache.P, sizeof(Blk<T>));
+__device__ __forceinline__ void stage_strip(const KParams<T>& kp, WarpSlot<T>& ws, int blk) {
+  if (blk == ws.blk) return;
   __syncwarp();
-  const ScenDev sc = cache.sc;
-  const bool active = (long long)s < sc.remaining;
-  const int p = (int)((sc.base + s) & 1);
-  const Blk<T>& b = H.b;
-  const int x0 = td.x0, y0 = td.y0;
-  const int ye = min(y0 + kp.ty, b.ny);
-  const int cbeg = passB ? x0 - 4 : x0;
-  const int cend = min(x0 + kp.tx + 4, b.pitch - kXOff);
-  const int ncol = cend - cbeg;
-  const int rbeg = passB ? y0 - 2 : y0;
-  const int nrow = passB ? min(ye + 2, b.ny + 3) - rbeg : ye - y0;
-  const int SW = L.SW;
-  // field list: (source array, element size, shared offset in bytes, rows)
-  const T* src[5];
-  size_t off[5];
-  int rows[5], esz[5];
-  const size_t plane = (size_t)SW * L.SH;
-  if (!passB) {
-    src[0] = b.eta[p]; src[1] = b.M[p]; src[2] = b.N[p]; src[3] = b.h; src[4] = b.emax;
-    const size_t ty1 = (size_t)SW * kp.ty * sizeof(T);
-    off[0] = 0; off[1] = ty1; off[2] = 2 * ty1; off[3] = 3 * ty1 + SW * sizeof(T);
-    off[4] = 4 * ty1 + SW * sizeof(T);
-    rows[0] = rows[1] = rows[3] = rows[4] = nrow;
-    rows[2] = nrow + 1;
-    esz[0] = esz[1] = esz[2] = esz[3] = esz[4] = sizeof(T);
-  } else {
-    src[0] = b.eta[p ^ 1]; src[1] = b.h; src[2] = b.M[p]; src[3] = b.N[p];
-    src[4] = reinterpret_cast<const T*>(b.man);
-    for (int f = 0; f < 4; ++f) off[f] = f * plane * sizeof(T);
-    off[4] = 4 * plane * sizeof(T);
-    for (int f = 0; f < 5; ++f) rows[f] = nrow;
-    esz[0] = esz[1] = esz[2] = esz[3] = sizeof(T);
-    esz[4] = sizeof(float);
-  }
-  unsigned total = 0;
-  for (int f = 0; f < 5; ++f) total += (unsigned)(rows[f] * ncol * esz[f]);
-  if (lane == 0) {
-    H.td = td;
-    H.p = p;
-    H.sn = (int)(sc.base + s + 1);
-    H.active = active;
-    mbar_arrive_tx(bar, active ? total : 0u);
+  warp_copy<T>(&ws.b, &RTI_BLK(kp, blk), sizeof(Blk<T>));
+  __syncwarp();
+  if (ws.b.is_child) warp_copy<T>(&ws.P, &RTI_BLK(kp, ws.b.parent), sizeof(Blk<T>));
+  if (threadIdx.x == 0) {
+    ws.sc = kp.scen[ws.b.scen];
+    ws.blk = blk;
   }
   __syncwarp();
-  if (!active) return;
-  int ncopy = 0;
-  for (int f = 0; f < 5; ++f) ncopy += rows[f];
-  for (int k = lane; k < ncopy; k += 32) {
-    int f = 0, r = k;
-    while (r >= rows[f]) r -= rows[f++];
-    const int gr = rbeg + r;
-    const char* g = reinterpret_cast<const char*>(src[f]) +
-                    ((size_t)(gr + kYOff) * b.pitch + (size_t)(cbeg + kXOff)) * esz[f];
-    unsigned char* d = stage + off[f] + (size_t)r * SW * esz[f];
-    bulk_g2s(d, g, (unsigned)(ncol * esz[f]), bar);
-  }
 }
 
-// pass A on a staged tile (see issue_tile for the layout)
+// Prepass of a strip over the region its march recomputes (rows y0-2..ye, the warp's
+// 32 columns, N up to row ye+1). A child's edge faces get the parent's current fluxes
+// (R7), stored into the child's own level-p arrays, whose edge entries nothing else
+// reads; a parent's ring cells get their fine-to-coarse eta^{n+1} or "none" (R8) in the
+// ring plane. Strips that overlap store the same values, and every lane later reads
+// back only what it stored itself. Kept out of line so that the march's registers do
+// not pay for the nesting arithmetic.
 template <class T>
-__device__ void pass_a_compute(const KParams<T>& kp, StepShared& sh, const SlotHdr<T>& H,
-                               const unsigned char* stage, const PipeLayout& L) {
-  const Blk<T>& b = H.b;
-  const Blk<T>& P = H.P;
-  const Tile td = H.td;
-  const int p = H.p, q = p ^ 1, sn = H.sn, SW = L.SW;
-  const T* sE = reinterpret_cast<const T*>(stage);
-  const T* sM = sE + (size_t)SW * kp.ty;
-  const T* sN = sM + (size_t)SW * kp.ty;
-  const T* sH = sN + (size_t)SW * (kp.ty + 1);
-  const T* sX = sH + (size_t)SW * kp.ty;
-  const bool child = b.is_child;
-  T vol_t = T(0);  // this thread's cells; the tile reduction below is binary64
-  double clip = 0.0, out = 0.0, ring = 0.0;
+__device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<T>& ws, Tile td,
+                                           int p) {
+  const Blk<T>& b = ws.b;
+  const int nx = b.nx, ny = b.ny, pitch = b.pitch;
+  const int c = td.x0 - 2 + (int)threadIdx.x;
+  const int y0 = td.y0, ye = min(y0 + kp.ty, ny);
+  const bool ring_strip = (td.flags & kTfRing) != 0;
+  const bool pull_strip =
+      b.is_child && (td.x0 == 0 || td.x0 + 29 >= nx || y0 - 2 <= 0 || ye + 1 >= ny);
+  size_t o = (size_t)(y0 - 2 + kYOff) * (size_t)pitch + (size_t)(c + kXOff);
+  for (int r = y0 - 2; r <= ye; ++r, o += pitch) {
+    if (pull_strip) {
+      if ((c == 0 || c == nx) && r >= 0 && r < ny) b.M[p][o] = face_m(b, ws.P, p, c, r);
+      if ((r + 1 == 0 || r + 1 == ny) && c >= 0 && c < nx)
+        b.N[p][o + pitch] = face_n(b, ws.P, p, c, r + 1);
+    }
+    if (ring_strip && c >= 0 && c < nx && r >= 0 && r < ny) {
+      T rv;
+      const int k = ring_value(kp, b, p, c, r, b.h[o], rv);
+      if (k) b.ring[o] = k == 2 ? rv : ring_none(rv);
+    }
+  }
+  __syncwarp();
+}
+
+// Step strip td at chunk step s (one warp; ws holds the strip's staged descriptor, the
+// prepass has run). The budget slot of the strip receives sum(eta^{n+1}) and adds the
+// clip, outflow and ring terms.
+template <class T>
+__device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& ws, Tile td,
+                                            int s) {
+  const int lane = threadIdx.x;
+  const Blk<T>& b = ws.b;
+  const ScenDev sc = ws.sc;
+  const int p = (int)((sc.base + s) & 1), q = p ^ 1;
+  const int sn = (int)(sc.base + s + 1);
+  // the descriptor fields of the march, as locals
+  const int nx = b.nx, ny = b.ny, pitch = b.pitch;
+  const bool root = !b.is_child;
+  const T dtdx = b.dtdx, eps = b.eps, g = b.g, cfric = b.cfric, dx = b.dx, q4dt = b.q4dt;
+  const T thr = b.thr;
+  const double volc = b.vol, dx2 = b.dx2;
+  const int bcW = b.bc[0], bcE = b.bc[1], bcS = b.bc[2], bcN = b.bc[3];
+  const T* etaP = b.eta[p];
+  const T* Mp = b.M[p];
+  const T* Np = b.N[p];
+  const T* hh = b.h;
+  const float* man = b.man;
+  const T* ringp = b.ring;
+  T* etaQ = b.eta[q];
+  T* Mq = b.M[q];
+  T* Nq = b.N[q];
+  T* emax = b.emax;
+  int* arr = b.arr;
+  const bool ring_strip = (td.flags & kTfRing) != 0;
+  const unsigned full = 0xffffffffu;
+
+  const int c = td.x0 - 2 + lane;                            // this lane's column (>= -2)
+  const bool col_ok = c + kXOff < pitch;                     // inside the allocated row
+  const bool own_col = lane >= 2 && lane < 2 + kStripW && c < nx;
+  const int y0 = td.y0, ye = min(y0 + kp.ty, ny);
+  double& clip = ws.acc[0][lane];  // this lane's binary64 budget partials
+  double& outf = ws.acc[1][lane];
+  double& ring = ws.acc[2][lane];
+  clip = 0.0;
+  outf = 0.0;
+  ring = 0.0;
+  T vol_t = T(0);
   bool bad = false;
-  const int xe = min(td.x0 + kp.tx, b.nx), ye = min(td.y0 + kp.ty, b.ny);
-  for (int j = td.y0 + threadIdx.y; j < ye; j += 8) {
-    for (int i = td.x0 + threadIdx.x; i < xe; i += 32) {
-      const int k = (j - td.y0) * SW + (i - td.x0);
-      const T Mw = (child && i == 0) ? face_m(b, P, p, 0, j) : sM[k];
-      const T Me = (child && i == b.nx - 1) ? face_m(b, P, p, b.nx, j) : sM[k + 1];
-      const T Ns = (child && j == 0) ? face_n(b, P, p, i, 0) : sN[k];
-      const T Nn = (child && j == b.ny - 1) ? face_n(b, P, p, i, b.ny) : sN[k + SW];
-      if (child) {  // store the pulled edge fluxes for pass B
-        if (i == 0) b.M[p][ix(b, 0, j)] = Mw;
-        if (i == b.nx - 1) b.M[p][ix(b, b.nx, j)] = Me;
-        if (j == 0) b.N[p][ix(b, i, 0)] = Ns;
-        if (j == b.ny - 1) b.N[p][ix(b, i, b.ny)] = Nn;
+  size_t o = (size_t)(y0 - 2 + kYOff) * (size_t)pitch + (size_t)(c + kXOff);
+
+  // prologue: N^n of y-face (c, y0 - 2) and the raw rows y0 - 2, y0 - 1
+  T nS = col_ok ? __ldcg(Np + o) : T(0);  // y0 - 2 is below row 0 or an interior row
+  T nSL = __shfl_up_sync(full, nS, 1);
+  Raw<T> R0 = load_raw(etaP, hh, Mp, Np, emax, man, o, pitch, col_ok);
+  Raw<T> R1 = load_raw(etaP, hh, Mp, Np, emax, man, o + pitch, pitch, col_ok);
+  Row<T> A = {}, B = {}, C = {};  // rows r-2, r-1, r once row r is formed
+
+  for (int r = y0 - 2; r <= ye; ++r, o += pitch) {
+    const Raw<T> cur = R0;
+    R0 = R1;
+    if (r + 2 <= ye) R1 = load_raw(etaP, hh, Mp, Np, emax, man, o + 2 * (size_t)pitch, pitch, col_ok);
+
+    // ---- row r: eta^{n+1} (R1, R5, R7 pulls, R8 ring) and the output update (R9)
+    Row<T> Nw;
+    const T m = cur.m, nn = cur.nn;  // a child's edge faces hold the pulled fluxes
+    Nw.H = cur.h;
+    Nw.MX = m;
+    Nw.NY = nS;
+    Nw.nm = cur.nm;
+    Nw.mE = __shfl_down_sync(full, m, 1);
+    const T nnL = __shfl_up_sync(full, nn, 1);
+    T e = cur.e - (dtdx * (Nw.mE - m) + dtdx * (nn - nS));
+    const bool own = own_col && r >= y0 && r < ye;
+    if (Nw.H + e < T(0)) {
+      if (own) clip += (double)(-Nw.H - e) * dx2;
+      e = -Nw.H;
+    }
+    if (ring_strip) {  // fine-to-coarse override (R8), formed by the prepass
+      const T rv = col_ok ? __ldcg(ringp + o) : ring_none(T(0));
+      if (!ring_unset(rv) && c >= 0 && c < nx && r >= 0 && r < ny) {
+        if (own) ring += ((double)rv - (double)e) * dx2;
+        e = rv;
       }
-      const T h = sH[k];
-      T e = sE[k] - (b.dtdx * (Me - Mw) + b.dtdx * (Nn - Ns));
-      if (h + e < T(0)) {
-        clip += (double)(-h - e) * b.dx2;
-        e = -h;
-      }
-      if (td.flags & kTfRing) {
-        T rv;
-        if (ring_value(kp, b, p, i, j, h, rv)) {
-          ring += ((double)rv - (double)e) * b.dx2;
-          e = rv;
-        }
-      }
-      const size_t c = ix(b, i, j);
-      b.eta[q][c] = e;
-      const T em = sX[k];
-      if (h + e > b.eps && e > em) {
-        if (em < b.thr && e >= b.thr) b.arr[c] = sn;
-        b.emax[c] = e;
+    }
+    Nw.E = e;
+    if (own) {
+      etaQ[o] = e;
+      const T em = cur.em;
+      if (Nw.H + e > eps && e > em) {
+        if (em < thr && e >= thr) arr[o] = sn;
+        emax[o] = e;
       }
       vol_t += e;
-      if (i == 0) out += b.vol * (double)(-Mw);
-      if (i == b.nx - 1) out += b.vol * (double)Me;
-      if (j == 0) out += b.vol * (double)(-Ns);
-      if (j == b.ny - 1) out += b.vol * (double)Nn;
       bad |= !dfinite(e);
+      if (c == 0) outf += volc * (double)(-m);
+      if (c == nx - 1) outf += volc * (double)Nw.mE;
+      if (r == 0) outf += volc * (double)(-nS);
+      if (r == ny - 1) outf += volc * (double)nn;
+    }
+
+    // ---- advective face terms of row r
+    Nw.eL = __shfl_up_sync(full, e, 1);
+    Nw.hL = __shfl_up_sync(full, Nw.H, 1);
+    {  // x-face (c, r)
+      const T dep = T(0.5) * (Nw.hL + Nw.H) + T(0.5) * (Nw.eL + Nw.E);
+      const bool in = c >= 1 && c <= nx - 1 && r >= 0 && r <= ny - 1;
+      Nw.vx = in && dep > eps;
+      Nw.nb = T(0.25) * ((nSL + nS) + (nnL + nn));
+      Nw.QX = T(0);
+      Nw.RX = T(0);
+      if (in && dep != T(0)) {
+        Nw.QX = Ar<T>::quot(m * m, dep);
+        Nw.RX = Ar<T>::quot(m * Nw.nb, dep);
+      }
+    }
+    {  // y-face (c, r)
+      const T dep = T(0.5) * (C.H + Nw.H) + T(0.5) * (C.E + Nw.E);
+      const bool in = r >= 1 && r <= ny - 1 && c >= 0 && c <= nx - 1;
+      Nw.vy = in && dep > eps;
+      Nw.mb = T(0.25) * ((C.MX + m) + (C.mE + Nw.mE));
+      Nw.SY = T(0);
+      Nw.TY = T(0);
+      if (in && dep != T(0)) {
+        Nw.SY = Ar<T>::quot(nS * nS, dep);
+        Nw.TY = Ar<T>::quot(nS * Nw.mb, dep);
+      }
+    }
+    A = B;
+    B = C;
+    C = Nw;
+    nS = nn;
+    nSL = nnL;
+
+    // ---- row j = r - 1: M^{n+1}, N^{n+1} (R2-R4) and the root edges (R6)
+    if (r > y0) {
+      const int j = r - 1;
+      const T qm = __shfl_up_sync(full, B.QX, 1), qp = __shfl_down_sync(full, B.QX, 1);
+      const T tw = __shfl_up_sync(full, B.TY, 1), te = __shfl_down_sync(full, B.TY, 1);
+      const float nmL = __shfl_up_sync(full, B.nm, 1);
+      const unsigned bx = __ballot_sync(full, B.vx), by = __ballot_sync(full, B.vy);
+      if (own_col) {
+        const size_t oj = o - (size_t)pitch;
+        const T xm = xmom_r(B.hL, B.eL, B.H, B.E, B.MX, B.nb, lane_bit(bx, lane, -1), qm, B.QX,
+                            lane_bit(bx, lane, 1), qp, A.vx, A.RX, B.RX, C.vx, C.RX, nmL, B.nm,
+                            eps, dtdx, g, cfric, dx, q4dt);
+        const T ym = ymom_r(A.H, A.E, B.H, B.E, B.NY, B.mb, A.vy, A.SY, B.SY, C.vy, C.SY,
+                            lane_bit(by, lane, -1), tw, B.TY, lane_bit(by, lane, 1), te, A.nm,
+                            B.nm, eps, dtdx, g, cfric, dx, q4dt);
+        if (c >= 1) Mq[oj] = xm;
+        else if (root) Mq[oj] = bcW == kBcRadiation ? radiate_r(B.H, B.E, T(-1), eps, g) : T(0);
+        if (c == nx - 1 && root)
+          Mq[oj + 1] = bcE == kBcRadiation ? radiate_r(B.H, B.E, T(1), eps, g) : T(0);
+        if (j >= 1) Nq[oj] = ym;
+        else if (root) Nq[oj] = bcS == kBcRadiation ? radiate_r(B.H, B.E, T(-1), eps, g) : T(0);
+        if (j == ny - 1 && root)
+          Nq[oj + pitch] = bcN == kBcRadiation ? radiate_r(B.H, B.E, T(1), eps, g) : T(0);
+      }
     }
   }
+
+  // ---- the strip's budget partials (binary64, fixed reduction order)
   if (bad) atomicOr(b.status, kStNonFinite);
-  const double vol = warp_sum((double)vol_t);
-  clip = warp_sum(clip);
-  out = warp_sum(out);
-  ring = warp_sum(ring);
-  const int w = threadIdx.y;
-  if (threadIdx.x == 0) {
-    sh.red[0][w] = vol;
-    sh.red[1][w] = clip;
-    sh.red[2][w] = out;
-    sh.red[3][w] = ring;
+  const double vs = warp_sum((double)vol_t);
+  const double cs = warp_sum(clip), os = warp_sum(outf), rs = warp_sum(ring);
+  if (lane == 0) {
+    double* slot = b.budget + 4 * (size_t)((y0 / kp.ty) * b.tiles_x + td.x0 / kp.tx);
+    slot[0] = vs;
+    slot[1] += cs;
+    slot[2] += os;
+    slot[3] += rs;
   }
-  __syncthreads();
-  if (threadIdx.y == 0 && threadIdx.x < 4) {
-    double a = 0.0;
-    for (int k = 0; k < 8; ++k) a += sh.red[threadIdx.x][k];
-    double* slot = b.budget + 4 * (size_t)((td.y0 / kp.ty) * b.tiles_x + td.x0 / kp.tx);
-    if (threadIdx.x == 0) slot[0] = a;
-    else slot[threadIdx.x] += a;
-  }
-}
-
-// pass B on a staged tile: face terms into the derived arrays, then the face updates
-template <class T>
-__device__ void pass_b_compute(const KParams<T>& kp, const SlotHdr<T>& H, unsigned char* stage,
-                               unsigned char* derived, const PipeLayout& L) {
-  const Blk<T>& b = H.b;
-  const Tile td = H.td;
-  const int p = H.p, q = p ^ 1;
-  const int W = L.SW;
-  const size_t n = (size_t)L.SW * L.SH;
-  BTile<T> S;
-  S.W = W;
-  T* st = reinterpret_cast<T*>(stage);
-  S.E = st;
-  S.H = st + n;
-  S.MX = st + 2 * n;
-  S.NY = st + 3 * n;
-  S.NM = reinterpret_cast<float*>(st + 4 * n);
-  T* dv = reinterpret_cast<T*>(derived);
-  S.QX = dv;
-  S.RX = dv + n;
-  S.SY = dv + 2 * n;
-  S.TY = dv + 3 * n;
-  S.VX = reinterpret_cast<unsigned char*>(dv + 4 * n);
-  S.VY = S.VX + n;
-  const int ox = td.x0 - 4, oy = td.y0 - 2;  // global (c, r) of local (0, 0)
-  // face terms of columns x0-1..x0+tx and rows y0-1..y0+ty
-  for (int ly = 1 + threadIdx.y; ly <= kp.ty + 2; ly += 8) {
-    for (int lx = 3 + threadIdx.x; lx <= kp.tx + 4; lx += 32) {
-      const int k = ly * W + lx;
-      const int c = ox + lx, r = oy + ly;
-      {  // x-face (c, r)
-        const T dep = T(0.5) * (S.H[k - 1] + S.H[k]) + T(0.5) * (S.E[k - 1] + S.E[k]);
-        const bool interior = c >= 1 && c <= b.nx - 1 && r >= 0 && r <= b.ny - 1;
-        S.VX[k] = interior && dep > b.eps;
-        if (interior && dep != T(0)) {
-          const T mm = S.MX[k];
-          const T nb = T(0.25) * ((S.NY[k - 1] + S.NY[k]) + (S.NY[k - 1 + W] + S.NY[k + W]));
-          S.QX[k] = Ar<T>::quot(mm * mm, dep);
-          S.RX[k] = Ar<T>::quot(mm * nb, dep);
-        }
-      }
-      {  // y-face (c, r)
-        const T dep = T(0.5) * (S.H[k - W] + S.H[k]) + T(0.5) * (S.E[k - W] + S.E[k]);
-        const bool interior = r >= 1 && r <= b.ny - 1 && c >= 0 && c <= b.nx - 1;
-        S.VY[k] = interior && dep > b.eps;
-        if (interior && dep != T(0)) {
-          const T v = S.NY[k];
-          const T mb = T(0.25) * ((S.MX[k - W] + S.MX[k]) + (S.MX[k - W + 1] + S.MX[k + 1]));
-          S.SY[k] = Ar<T>::quot(v * v, dep);
-          S.TY[k] = Ar<T>::quot(v * mb, dep);
-        }
-      }
-    }
-  }
-  __syncthreads();
-  T* Mo = b.M[q];
-  T* No = b.N[q];
-  const bool root = !b.is_child;
-  const int xe = min(td.x0 + kp.tx, b.nx), ye = min(td.y0 + kp.ty, b.ny);
-  for (int j = td.y0 + threadIdx.y; j < ye; j += 8) {
-    for (int i = td.x0 + threadIdx.x; i < xe; i += 32) {
-      const int k = (j - oy) * W + (i - ox);
-      if (i >= 1) {
-        Mo[ix(b, i, j)] = xmom_s(b, S, k);
-      } else if (root) {
-        Mo[ix(b, 0, j)] = b.bc[0] == kBcRadiation ? radiate_s(b, S, k, T(-1)) : T(0);
-      }
-      if (i == b.nx - 1 && root)
-        Mo[ix(b, b.nx, j)] = b.bc[1] == kBcRadiation ? radiate_s(b, S, k, T(1)) : T(0);
-      if (j >= 1) {
-        No[ix(b, i, j)] = ymom_s(b, S, k);
-      } else if (root) {
-        No[ix(b, i, 0)] = b.bc[2] == kBcRadiation ? radiate_s(b, S, k, T(-1)) : T(0);
-      }
-      if (j == b.ny - 1 && root)
-        No[ix(b, i, b.ny)] = b.bc[3] == kBcRadiation ? radiate_s(b, S, k, T(1)) : T(0);
-    }
-  }
-}
-
-// One pass over this CTA's tiles (t = blockIdx.x + k * gridDim.x) with two stages.
-// Returns false when a wait ran out (kStTimeout recorded, copies drained).
-template <class T>
-__device__ bool run_pass(const KParams<T>& kp, StepShared& sh, unsigned char* dsm,
-                         const PipeLayout& L, unsigned& phase, int s, bool passB) {
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(dsm);
-  SlotHdr<T>* hdr = reinterpret_cast<SlotHdr<T>*>(dsm + 2 * sizeof(unsigned long long));
-  unsigned char* stg[2] = {dsm + L.hdr, dsm + L.hdr + L.stage};
-  unsigned char* derived = dsm + L.hdr + 2 * L.stage;
-  IssueCache<T>& cache = *reinterpret_cast<IssueCache<T>*>(
-      dsm + 2 * sizeof(unsigned long long) + 2 * sizeof(SlotHdr<T>));
-  const int nt = *kp.ntiles;
-  const int G = gridDim.x;
-  const bool issuer = threadIdx.y == 0;
-  int t = blockIdx.x;
-  if (issuer && t < nt) {
-    fence_proxy_async();  // earlier generic writes (other CTAs, previous pass) before the copies
-    issue_tile(kp, t, s, passB, hdr[0], cache, stg[0], &bar[0], L);
-  }
-  for (int k = 0; t < nt; ++k, t += G) {
-    const int st = k & 1;
-    if (issuer && t + G < nt) {
-      fence_proxy_async();  // this CTA's reads of the other stage before its refill
-      issue_tile(kp, t + G, s, passB, hdr[st ^ 1], cache, stg[st ^ 1], &bar[st ^ 1], L);
-    }
-    const unsigned par = (phase >> st) & 1u;
-    bool ok = mbar_wait(&bar[st], par, kp.spin_cycles);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(kp.status, kStTimeout);
-      mbar_wait(&bar[st], par, kp.spin_cycles);  // drain before leaving
-      if (issuer && t + G < nt) mbar_wait(&bar[st ^ 1], (phase >> (st ^ 1)) & 1u, kp.spin_cycles);
-      return false;
-    }
-    phase ^= 1u << st;
-    if (hdr[st].active) {
-      if (passB) pass_b_compute(kp, hdr[st], stg[st], derived, L);
-      else pass_a_compute(kp, sh, hdr[st], stg[st], L);
-    }
-    __syncthreads();  // stage st and its header are free again
-  }
-  return true;
-}
-
-template <class T>
-__device__ __forceinline__ void init_pipe(unsigned char* dsm) {
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(dsm);
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    reinterpret_cast<IssueCache<T>*>(dsm + 2 * sizeof(unsigned long long) +
-                                     2 * sizeof(SlotHdr<T>))->blk = -1;
-  }
-  __syncthreads();
 }
 
 // ------------------------------------------------------------------ device-wide barrier
@@ -815,44 +667,35 @@ __device__ __forceinline__ bool grid_barrier(Bar* bar, unsigned& gen, int* statu
 }
 
 // ------------------------------------------------------------------ kernels
-// Dynamic shared memory of the step kernels: pipe_layout<T>(tx, ty).total bytes.
+// Steps [s_first, s_first + s_count) of a chunk over every strip of the work list; the
+// warps take strips round-robin. With more than one step the launch must be
+// cooperative: consecutive steps are separated by the device-wide barrier.
 template <class T>
-__global__ void __launch_bounds__(256) k_persistent(KParams<T> kp) {
-  __shared__ StepShared sh;
-  extern __shared__ __align__(128) unsigned char dsm[];
-  const PipeLayout L = pipe_layout<T>(kp.tx, kp.ty);
-  init_pipe<T>(dsm);
-  unsigned phase = 0;
+__global__ void __launch_bounds__(256) k_step(KParams<T> kp, int s_first, int s_count) {
+  __shared__ WarpSlot<T> slots[8];
+  __shared__ int go;
+  WarpSlot<T>& ws = slots[threadIdx.y];
+  if (threadIdx.x == 0) ws.blk = -1;
+  __syncwarp();
   unsigned gen = 0;
-  if (threadIdx.x == 0 && threadIdx.y == 0) gen = ld_acquire_u32(&kp.bar->gen);
-  for (int s = 0; s < kp.nsteps; ++s) {
-    if (!run_pass(kp, sh, dsm, L, phase, s, false)) return;
-    if (!grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &sh.go)) return;
-    if (!run_pass(kp, sh, dsm, L, phase, s, true)) return;
-    if (s + 1 < kp.nsteps && !grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &sh.go))
+  if (s_count > 1 && threadIdx.x == 0 && threadIdx.y == 0) gen = ld_acquire_u32(&kp.bar->gen);
+  const int nt = *kp.ntiles;
+  const int G = gridDim.x * 8;
+  for (int s = s_first; s < s_first + s_count; ++s) {
+    for (int t = blockIdx.x * 8 + threadIdx.y; t < nt; t += G) {
+      const Tile td = kp.tiles[t];
+      stage_strip(kp, ws, td.blk);
+      if ((long long)s >= ws.sc.remaining) continue;  // the scenario has finished
+      if ((td.flags & kTfRing) || ws.b.is_child)
+        strip_prepass(kp, ws, td, (int)((ws.sc.base + s) & 1));
+      march_strip(kp, ws, td, s);
+    }
+    if (s + 1 < s_first + s_count &&
+        !grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go))
       return;
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_pass_a(KParams<T> kp, int s) {
-  __shared__ StepShared sh;
-  extern __shared__ __align__(128) unsigned char dsm[];
-  const PipeLayout L = pipe_layout<T>(kp.tx, kp.ty);
-  init_pipe<T>(dsm);
-  unsigned phase = 0;
-  run_pass(kp, sh, dsm, L, phase, s, false);
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_pass_b(KParams<T> kp, int s) {
-  __shared__ StepShared sh;
-  extern __shared__ __align__(128) unsigned char dsm[];
-  const PipeLayout L = pipe_layout<T>(kp.tx, kp.ty);
-  init_pipe<T>(dsm);
-  unsigned phase = 0;
-  run_pass(kp, sh, dsm, L, phase, s, true);
-}
 
 // sum(eta) of every tile at the current level (after an initial condition or a restore)
 template <class T>

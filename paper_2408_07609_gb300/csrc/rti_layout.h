@@ -14,6 +14,7 @@ namespace rti {
 constexpr int kXOff = 4;       // margin columns before column 0
 constexpr int kYOff = 2;       // margin rows before row 0 and after row ny
 constexpr int kPitchAlign = 32; // elements
+constexpr int kStripW = 28;    // owned columns of a strip: a warp's 32 lanes less a 2-column halo each side
 constexpr double kNeverWet = -1.0e30;
 
 enum : int { kBcWall = 0, kBcRadiation = 1 };
@@ -37,6 +38,8 @@ struct Blk {
   const float* man;
   T* emax;    // max eta over wet instants (kNeverWet until wet)
   int* arr;   // arrival step, -1 if never
+  T* ring;    // a parent's fine-to-coarse eta^{n+1} on ring cells, all-ones bits elsewhere
+              // (written each step by the strips that read it); null without children
   int nx, ny, pitch, parent; // parent: index in the batch block table, -1 for a root
   int i0, j0;                // child origin in parent cells
   int child_first, child_count; // children: kids[child_first .. +child_count)

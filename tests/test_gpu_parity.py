@@ -67,7 +67,7 @@ def test_ragged_single_grid_fp64(rti, oracle_mod):
         compare_fp64(h, o, 1)
 
 
-@pytest.mark.parametrize("tile", [(32, 8), (64, 16), (128, 8)])
+@pytest.mark.parametrize("tile", [(28, 8), (28, 16), (28, 64)])
 def test_tile_shapes_bitwise_equal(rti, oracle_mod, tile):
     sc = S.config1(nx=150, ny=90, steps=200)
     h, o = run_pair(rti, oracle_mod, sc, sc.steps, tile=tile)

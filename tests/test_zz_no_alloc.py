@@ -94,12 +94,31 @@ def test_noalloc_matches_rti_step_on_two_calls(rti, precision, schedule):
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(rti):
-    big = dict(level=1, parent=-1, nx=2112, ny=2000, i0=0, j0=0, dx=1000.0, bc=(0, 0, 0, 0))
+    """8192^2 cells are 37,504 strips of 28 x 64, far above the 4096-strip scratch: the
+    call returns before any device work. The arrays are host memory, which the second
+    host check (device memory only) would refuse as well, so no launch can follow."""
+    big = dict(level=1, parent=-1, nx=8192, ny=8192, i0=0, j0=0, dx=1000.0, bc=(0, 0, 0, 0))
+    host = np.zeros(1 << 10, dtype=np.float64)
     st = rti.NoAllocState()
     for q in range(2):
-        st.eta[q] = st.M[q] = st.N[q] = 256
-    st.h = st.manning = st.max_eta = st.arrival_step = 256
-    st.pitch = rti.noalloc_pitch(2112)
+        st.eta[q] = st.M[q] = st.N[q] = host.ctypes.data
+    st.h = st.manning = st.max_eta = st.arrival_step = host.ctypes.data
+    st.pitch = rti.noalloc_pitch(8192)
     with pytest.raises(rti.RtiError) as ei:
-        rti.step_noalloc(big, rti.make_params(1.0), st, 0, 1)
+        rti.step_noalloc(big, rti.make_params(1.0, tile=(28, 64)), st, 0, 1)
     assert ei.value.code == -1 and "tiles exceeds" in str(ei.value)
+
+
+def test_noalloc_rejects_host_addresses(rti):
+    """A grid that fits the scratch but whose arrays are not device memory is refused
+    on the host, before any launch."""
+    small = dict(level=1, parent=-1, nx=64, ny=64, i0=0, j0=0, dx=1000.0, bc=(0, 0, 0, 0))
+    host = np.zeros(1 << 16, dtype=np.float64)
+    st = rti.NoAllocState()
+    for q in range(2):
+        st.eta[q] = st.M[q] = st.N[q] = host.ctypes.data
+    st.h = st.manning = st.max_eta = st.arrival_step = host.ctypes.data
+    st.pitch = rti.noalloc_pitch(64)
+    with pytest.raises(rti.RtiError) as ei:
+        rti.step_noalloc(small, rti.make_params(1.0), st, 0, 1)
+    assert ei.value.code == -1 and "not device memory" in str(ei.value)
