@@ -70,7 +70,7 @@ typedef struct {
   int schedule;       /* RTI_SCHED_* */
   int tile_x;         /* strip width in cells: 0 or 28 (a warp's 32 lanes less a 2-cell halo
                          on each side); other values are RTI_ERR_INVALID_ARG */
-  int tile_y;         /* strip height in cells, a multiple of 8; 0 = 32 */
+  int tile_y;         /* strip height in cells, a multiple of 8; 0 = 64 */
 } rti_params;
 
 typedef struct rti_handle rti_handle;
@@ -148,7 +148,7 @@ const char* rti_error_string(int code);
  * list, counters, device barrier, status words, budget partials) from one file-scope
  * device array of about 200 KB that every GPU which loads the library holds until the
  * process exits. Limit: a single root grid (parent -1) of at most 4096 strips (2048 x 2048
- * cells make 4736 of 28 x 32 strips: use tile_y = 64 there); larger grids return RTI_ERR_INVALID_ARG and
+ * cells make 2368 of the default 28 x 64 strips); larger grids return RTI_ERR_INVALID_ARG and
  * rti_last_error(NULL) says why.
  *
  * State layout (element type double for RTI_FP64, float for RTI_FP32; manning is always

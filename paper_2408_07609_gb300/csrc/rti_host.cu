@@ -33,7 +33,7 @@ static thread_local std::string t_create_err;
 
 namespace {
 
-constexpr int kDefaultTx = kStripW, kDefaultTy = 32;
+constexpr int kDefaultTx = kStripW, kDefaultTy = 64;
 constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at the maximum SM clock
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -399,6 +399,14 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
       }
     }
   }
+  // strips with nesting work (a ring, or a child's edge) first: the step kernel hands
+  // strips out in list order, so the slow ones start early
+  std::stable_partition(tiles.begin(), tiles.end(), [&](const Tile& t) {
+    const Blk<T>& b = blks[t.blk];
+    const bool edge = b.is_child && (t.x0 == 0 || t.x0 + kStripW + 2 >= b.nx || t.y0 == 0 ||
+                                     t.y0 + g->ty + 2 >= b.ny);
+    return (t.flags & kTfRing) || edge;
+  });
   bool moved = false;
   cudaError_t e = grow(&g->d_blk, &g->cap_blk, blks.size() * sizeof(Blk<T>) + 64, &moved);
   if (e == cudaSuccess) e = grow(&g->d_kids, &g->cap_kids, kids.size() * sizeof(int) + 64, &moved);
@@ -1123,6 +1131,7 @@ __global__ void k_noalloc_setup(NoAllocScratch* s, Blk<T> b, int tx, int ty, int
     s->scen.remaining = nsteps;
     s->bar.count = 0;
     s->bar.gen = 0;
+    s->bar.next[0] = s->bar.next[1] = 0;
   }
 }
 

@@ -11,7 +11,7 @@ cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty) {
   int dev = 0, sms = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T>, 256, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T>, kWarps * 32, 0);
   if (e == cudaSuccess) *grid = sms * (per > 0 ? per : 1);
   return e;
 }
@@ -19,11 +19,10 @@ cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty) {
 template <>
 cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid,
                                 const int* nscen, cudaStream_t st) {
-  cudaError_t e = cudaSuccess;
-  const dim3 blk(32, 8);
+  const dim3 blk(32, kWarps);
+  cudaError_t e = cudaMemsetAsync(kp.bar, 0, sizeof(Bar), st);  // barrier and strip counters
+  if (e != cudaSuccess) return e;
   if (schedule == 0) {  // one cooperative launch for the whole chunk
-    e = cudaMemsetAsync(kp.bar, 0, sizeof(Bar), st);
-    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = blk;

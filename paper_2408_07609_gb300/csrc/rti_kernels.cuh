@@ -97,18 +97,23 @@ __device__ __forceinline__ void stage_blk(Blk<T>* dst, const Blk<T>* src) {
 }
 
 // ------------------------------------------------------------------ coarse -> fine (R7)
+// (2 v_k + v_n) / 3 in the state precision: binary64 as the oracle writes it, binary32
+// in binary32 (a binary64 divide costs dozens of slow FP64 instructions on this part).
+__device__ __forceinline__ double interp3(double vk, double vn) { return (2.0 * vk + vn) / 3.0; }
+__device__ __forceinline__ float interp3(float vk, float vn) { return (2.0f * vk + vn) / 3.0f; }
+
 // Fine face t of an edge whose coarse faces are v(k), k = 0..K-1: the coarse value at
 // the middle fine face, (2 v_k + v_{k+-1}) / 3 at the outer ones, neighbour clamped.
 template <class T>
-__device__ __noinline__ T edge_interp(const T* arr, const Blk<T>& P, int fixed, int start, int K,
-                                      int t, bool along_y) {
+__device__ __forceinline__ T edge_interp(const T* arr, const Blk<T>& P, int fixed, int start,
+                                         int K, int t, bool along_y) {
   int k = t / 3, sub = t - 3 * k;
-  double vk = along_y ? (double)arr[ix(P, fixed, start + k)] : (double)arr[ix(P, start + k, fixed)];
-  if (sub == 1) return (T)vk;
+  const T vk = along_y ? arr[ix(P, fixed, start + k)] : arr[ix(P, start + k, fixed)];
+  if (sub == 1) return vk;
   int kn = sub == 0 ? k - 1 : k + 1;
   kn = kn < 0 ? 0 : (kn > K - 1 ? K - 1 : kn);
-  double vn = along_y ? (double)arr[ix(P, fixed, start + kn)] : (double)arr[ix(P, start + kn, fixed)];
-  return (T)((2.0 * vk + vn) / 3.0);
+  const T vn = along_y ? arr[ix(P, fixed, start + kn)] : arr[ix(P, start + kn, fixed)];
+  return interp3(vk, vn);
 }
 
 // x-flux of face (f, j) at parity p; a child's edge faces come from its parent P.
@@ -154,36 +159,30 @@ __device__ T child_eta_next(const Blk<T>& c, const Blk<T>& P, int p, int x, int 
 }
 
 // ------------------------------------------------------------------ fine -> coarse (R8)
-// Parent cell (I, J) of block b: 0 if it is not on the inner ring of a child footprint,
-// 1 if it is but the 3x3 child patch has no wet cell, 2 if `out` holds the floored mean
-// of the patch's wet child levels at eta^{n+1} (recomputed from the child's level p).
+// Patch (u, v) of child c (parent cell (c.i0 + u, c.j0 + v) of block P, on the inner
+// ring of c's footprint): if the 3x3 child patch has a wet cell, `out` gets the mean of
+// the wet child levels at eta^{n+1} (recomputed from the child's level p; binary64
+// accumulator, Listing 5 order: x outer, y inner), floored at -hP.
 template <class T>
-__device__ __noinline__ int ring_value(const KParams<T>& kp, const Blk<T>& b, int p, int I, int J,
-                                       T hP, T& out) {
-  for (int q = 0; q < b.child_count; ++q) {
-    const Blk<T> c = RTI_BLK(kp, RTI_KID(kp, b.child_first + q));
-    int a = c.nx / 3, bb = c.ny / 3;
-    int u = I - c.i0, v = J - c.j0;
-    if (u < 0 || v < 0 || u >= a || v >= bb) continue;
-    if (!(u == 0 || u == a - 1 || v == 0 || v == bb - 1)) return 0;
-    double sum = 0.0;
-    int wet = 0;
-    for (int x = 3 * u; x < 3 * u + 3; ++x) {    // outer: x (the paper's J)
-      for (int y = 3 * v; y < 3 * v + 3; ++y) {  // inner: y (the paper's I)
-        T e = child_eta_next(c, b, p, x, y);
-        if (c.h[ix(c, x, y)] + e > c.eps) {
-          sum = sum + (double)e;
-          wet = wet + 1;
-        }
+__device__ bool ring_patch(const Blk<T>& c, const Blk<T>& P, int p, int u, int v, T hP, T& out) {
+  constexpr double kInvWet[10] = {0.0,       1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0,
+                                  1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0};
+  double sum = 0.0;
+  int wet = 0;
+  for (int x = 3 * u; x < 3 * u + 3; ++x) {    // outer: x (the paper's J)
+    for (int y = 3 * v; y < 3 * v + 3; ++y) {  // inner: y (the paper's I)
+      T e = child_eta_next(c, P, p, x, y);
+      if (c.h[ix(c, x, y)] + e > c.eps) {
+        sum = sum + (double)e;
+        wet = wet + 1;
       }
     }
-    if (wet == 0) return 1;
-    double avg = sum * (1.0 / (double)wet);
-    if (avg < -(double)hP) avg = -(double)hP;
-    out = (T)avg;
-    return 2;
   }
-  return 0;
+  if (wet == 0) return false;
+  double avg = sum * kInvWet[wet];  // = sum * (1.0 / wet): the table holds the rounded quotients
+  if (avg < -(double)hP) avg = -(double)hP;
+  out = (T)avg;
+  return true;
 }
 
 // "no override" in a ring plane: all-ones bits (a NaN that arithmetic never produces
@@ -242,9 +241,19 @@ __device__ __forceinline__ T flux_update(const Blk<T>& b, T m, T across, T Df, T
   return Ar<T>::update(m, across, Df, grad, adv, nf, b.g, b.dtdx, b.cfric);
 }
 
-template <class T>
-__device__ __forceinline__ T limit_outflow(T m, T Dlo, T Dhi, T dx, T q4dt) {
-  T cap = (m > T(0) ? Dlo : Dhi) * dx / q4dt;
+// Outflow limit: |flux| <= D dx / (4 dt) with D the depth of the cell it drains.
+// Binary64 keeps the oracle's expression; binary32 multiplies by dx / (4 dt), which the
+// compiler hoists out of the march.
+__device__ __forceinline__ double limit_outflow(double m, double Dlo, double Dhi, double dx,
+                                                double q4dt) {
+  const double cap = (m > 0.0 ? Dlo : Dhi) * dx / q4dt;
+  if (m > cap) return cap;
+  if (m < -cap) return -cap;
+  return m;
+}
+__device__ __forceinline__ float limit_outflow(float m, float Dlo, float Dhi, float dx,
+                                               float q4dt) {
+  const float cap = (m > 0.0f ? Dlo : Dhi) * (dx / q4dt);
   if (m > cap) return cap;
   if (m < -cap) return -cap;
   return m;
@@ -424,34 +433,69 @@ __device__ __forceinline__ void stage_strip(const KParams<T>& kp, WarpSlot<T>& w
   __syncwarp();
 }
 
-// Prepass of a strip over the region its march recomputes (rows y0-2..ye, the warp's
-// 32 columns, N up to row ye+1). A child's edge faces get the parent's current fluxes
-// (R7), stored into the child's own level-p arrays, whose edge entries nothing else
-// reads; a parent's ring cells get their fine-to-coarse eta^{n+1} or "none" (R8) in the
-// ring plane. Strips that overlap store the same values, and every lane later reads
-// back only what it stored itself. Kept out of line so that the march's registers do
+// Prepass of a strip over the region its march reads: columns x0-2..x0+29, rows
+// y0-2..ye of cells and x-faces, y-faces up to row ye+1. A child's edge faces there get
+// the parent's current fluxes (R7), stored into the child's own level-p arrays, whose
+// edge entries nothing else reads; a parent's ring cells there get their fine-to-coarse
+// eta^{n+1} or "none" (R8) in the ring plane. The items of the region are spread over
+// the lanes; strips that overlap store the same values, and __syncwarp orders the
+// stores before the march's loads. Kept out of line so that the march's registers do
 // not pay for the nesting arithmetic.
 template <class T>
 __device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<T>& ws, Tile td,
                                            int p) {
   const Blk<T>& b = ws.b;
-  const int nx = b.nx, ny = b.ny, pitch = b.pitch;
-  const int c = td.x0 - 2 + (int)threadIdx.x;
-  const int y0 = td.y0, ye = min(y0 + kp.ty, ny);
-  const bool ring_strip = (td.flags & kTfRing) != 0;
-  const bool pull_strip =
-      b.is_child && (td.x0 == 0 || td.x0 + 29 >= nx || y0 - 2 <= 0 || ye + 1 >= ny);
-  size_t o = (size_t)(y0 - 2 + kYOff) * (size_t)pitch + (size_t)(c + kXOff);
-  for (int r = y0 - 2; r <= ye; ++r, o += pitch) {
-    if (pull_strip) {
-      if ((c == 0 || c == nx) && r >= 0 && r < ny) b.M[p][o] = face_m(b, ws.P, p, c, r);
-      if ((r + 1 == 0 || r + 1 == ny) && c >= 0 && c < nx)
-        b.N[p][o + pitch] = face_n(b, ws.P, p, c, r + 1);
+  const int nx = b.nx, ny = b.ny;
+  const int lane = threadIdx.x;
+  const int ye = min(td.y0 + kp.ty, ny);
+  const int cx0 = td.x0 - 2, cx1 = td.x0 + 30;  // columns [cx0, cx1)
+  const int ry0 = td.y0 - 2, ry1 = ye + 1;      // cell rows [ry0, ry1); y-face rows [ry0, ry1]
+  if (b.is_child) {
+    const int r0 = max(ry0, 0), r1 = min(ry1, ny);
+    for (int side = 0; side < 2; ++side) {  // west / east faces M(f, r)
+      const int f = side ? nx : 0;
+      if (f < cx0 || f >= cx1) continue;
+      for (int r = r0 + lane; r < r1; r += 32) b.M[p][ix(b, f, r)] = face_m(b, ws.P, p, f, r);
     }
-    if (ring_strip && c >= 0 && c < nx && r >= 0 && r < ny) {
-      T rv;
-      const int k = ring_value(kp, b, p, c, r, b.h[o], rv);
-      if (k) b.ring[o] = k == 2 ? rv : ring_none(rv);
+    const int c0 = max(cx0, 0), c1 = min(cx1, nx);
+    for (int side = 0; side < 2; ++side) {  // south / north faces N(c, g)
+      const int g = side ? ny : 0;
+      if (g < ry0 || g > ry1) continue;
+      for (int c = c0 + lane; c < c1; c += 32) b.N[p][ix(b, c, g)] = face_n(b, ws.P, p, c, g);
+    }
+  }
+  if (td.flags & kTfRing) {
+    const int c0 = max(cx0, 0), c1 = min(cx1, nx), r0 = max(ry0, 0), r1 = min(ry1, ny);
+    for (int q = 0; q < b.child_count; ++q) {
+      const Blk<T> ch = RTI_BLK(kp, RTI_KID(kp, b.child_first + q));
+      const int a0 = ch.i0, a1 = ch.i0 + ch.nx / 3, b0 = ch.j0, b1 = ch.j0 + ch.ny / 3;
+      // the footprint's inner ring within the region: rows b0 and b1-1 (all columns),
+      // columns a0 and a1-1 (rows strictly between)
+      const int hc0 = max(c0, a0), hc1 = min(c1, a1), nh = max(hc1 - hc0, 0);
+      const int vr0 = max(r0, b0 + 1), vr1 = min(r1, b1 - 1), nv = max(vr1 - vr0, 0);
+      const bool rb = b0 >= r0 && b0 < r1, rt = b1 - 1 >= r0 && b1 - 1 < r1 && b1 - 1 != b0;
+      const bool cl = a0 >= c0 && a0 < c1, cr = a1 - 1 >= c0 && a1 - 1 < c1 && a1 - 1 != a0;
+      const int n0 = rb ? nh : 0, n1 = rt ? nh : 0, n2 = cl ? nv : 0, n3 = cr ? nv : 0;
+      for (int k = lane; k < n0 + n1 + n2 + n3; k += 32) {
+        int I, J;
+        if (k < n0) {
+          I = hc0 + k;
+          J = b0;
+        } else if (k < n0 + n1) {
+          I = hc0 + (k - n0);
+          J = b1 - 1;
+        } else if (k < n0 + n1 + n2) {
+          I = a0;
+          J = vr0 + (k - n0 - n1);
+        } else {
+          I = a1 - 1;
+          J = vr0 + (k - n0 - n1 - n2);
+        }
+        const size_t o = ix(b, I, J);
+        T rv;
+        const bool wet = ring_patch(ch, b, p, I - a0, J - b0, b.h[o], rv);
+        b.ring[o] = wet ? rv : ring_none(rv);
+      }
     }
   }
   __syncwarp();
@@ -492,6 +536,8 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   const int c = td.x0 - 2 + lane;                            // this lane's column (>= -2)
   const bool col_ok = c + kXOff < pitch;                     // inside the allocated row
   const bool own_col = lane >= 2 && lane < 2 + kStripW && c < nx;
+  const bool col_x = c >= 1 && c <= nx - 1;  // x-face (c, .) is interior
+  const bool col_y = c >= 0 && c <= nx - 1;  // y-face (c, .) lies on a cell column
   const int y0 = td.y0, ye = min(y0 + kp.ty, ny);
   double& clip = ws.acc[0][lane];  // this lane's binary64 budget partials
   double& outf = ws.acc[1][lane];
@@ -532,7 +578,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     }
     if (ring_strip) {  // fine-to-coarse override (R8), formed by the prepass
       const T rv = col_ok ? __ldcg(ringp + o) : ring_none(T(0));
-      if (!ring_unset(rv) && c >= 0 && c < nx && r >= 0 && r < ny) {
+      if (!ring_unset(rv) && col_y && r >= 0 && r < ny) {
         if (own) ring += ((double)rv - (double)e) * dx2;
         e = rv;
       }
@@ -558,7 +604,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     Nw.hL = __shfl_up_sync(full, Nw.H, 1);
     {  // x-face (c, r)
       const T dep = T(0.5) * (Nw.hL + Nw.H) + T(0.5) * (Nw.eL + Nw.E);
-      const bool in = c >= 1 && c <= nx - 1 && r >= 0 && r <= ny - 1;
+      const bool in = col_x && r >= 0 && r <= ny - 1;
       Nw.vx = in && dep > eps;
       Nw.nb = T(0.25) * ((nSL + nS) + (nnL + nn));
       Nw.QX = T(0);
@@ -570,7 +616,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     }
     {  // y-face (c, r)
       const T dep = T(0.5) * (C.H + Nw.H) + T(0.5) * (C.E + Nw.E);
-      const bool in = r >= 1 && r <= ny - 1 && c >= 0 && c <= nx - 1;
+      const bool in = col_y && r >= 1 && r <= ny - 1;
       Nw.vy = in && dep > eps;
       Nw.mb = T(0.25) * ((C.MX + m) + (C.mE + Nw.mE));
       Nw.SY = T(0);
@@ -667,12 +713,16 @@ __device__ __forceinline__ bool grid_barrier(Bar* bar, unsigned& gen, int* statu
 }
 
 // ------------------------------------------------------------------ kernels
-// Steps [s_first, s_first + s_count) of a chunk over every strip of the work list; the
-// warps take strips round-robin. With more than one step the launch must be
-// cooperative: consecutive steps are separated by the device-wide barrier.
+// Steps [s_first, s_first + s_count) of a chunk over every strip of the work list. The
+// warps take strips from a device counter per step (heavy strips come first in the
+// list), so a slow strip delays no fixed set of others. Counter s & 1 serves step s;
+// the other one is cleared during step s, when no warp can still be taking from it
+// (step s - 1 has ended: a barrier or the previous launch lies between). With more
+// than one step the launch must be cooperative: consecutive steps are separated by the
+// device-wide barrier.
 template <class T>
-__global__ void __launch_bounds__(256) k_step(KParams<T> kp, int s_first, int s_count) {
-  __shared__ WarpSlot<T> slots[8];
+__global__ void __launch_bounds__(kWarps * 32) k_step(KParams<T> kp, int s_first, int s_count) {
+  __shared__ WarpSlot<T> slots[kWarps];
   __shared__ int go;
   WarpSlot<T>& ws = slots[threadIdx.y];
   if (threadIdx.x == 0) ws.blk = -1;
@@ -680,9 +730,14 @@ __global__ void __launch_bounds__(256) k_step(KParams<T> kp, int s_first, int s_
   unsigned gen = 0;
   if (s_count > 1 && threadIdx.x == 0 && threadIdx.y == 0) gen = ld_acquire_u32(&kp.bar->gen);
   const int nt = *kp.ntiles;
-  const int G = gridDim.x * 8;
   for (int s = s_first; s < s_first + s_count; ++s) {
-    for (int t = blockIdx.x * 8 + threadIdx.y; t < nt; t += G) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+      atomicExch(&kp.bar->next[(s + 1) & 1], 0u);
+    for (;;) {
+      unsigned t = 0;
+      if (threadIdx.x == 0) t = atomicAdd(&kp.bar->next[s & 1], 1u);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t >= (unsigned)nt) break;
       const Tile td = kp.tiles[t];
       stage_strip(kp, ws, td.blk);
       if ((long long)s >= ws.sc.remaining) continue;  // the scenario has finished
@@ -695,7 +750,6 @@ __global__ void __launch_bounds__(256) k_step(KParams<T> kp, int s_first, int s_
       return;
   }
 }
-
 
 // sum(eta) of every tile at the current level (after an initial condition or a restore)
 template <class T>

@@ -14,6 +14,7 @@ namespace rti {
 constexpr int kXOff = 4;       // margin columns before column 0
 constexpr int kYOff = 2;       // margin rows before row 0 and after row ny
 constexpr int kPitchAlign = 32; // elements
+constexpr int kWarps = 4;      // warps per CTA of the step kernel
 constexpr int kStripW = 28;    // owned columns of a strip: a warp's 32 lanes less a 2-column halo each side
 constexpr double kNeverWet = -1.0e30;
 
@@ -67,6 +68,7 @@ struct ScenDev {
 struct Bar {
   unsigned int count;
   unsigned int gen;
+  unsigned int next[2];  // strip counters of the step kernel (step parity)
 };
 
 // One tile: cells [x0, x0+tx) x [y0, y0+ty) of block `blk`.
