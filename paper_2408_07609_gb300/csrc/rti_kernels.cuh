@@ -39,8 +39,14 @@ __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dcbrt(double x) { return cbrt(x); }
 __device__ __forceinline__ float dcbrt(float x) { return cbrtf(x); }
-__device__ __forceinline__ bool dfinite(double x) { return isfinite(x); }
-__device__ __forceinline__ bool dfinite(float x) { return isfinite(x); }
+// finite <=> the exponent field is not all ones (integer test, no conversions)
+__device__ __forceinline__ bool dfinite(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ULL) !=
+         0x7ff0000000000000ULL;
+}
+__device__ __forceinline__ bool dfinite(float x) {
+  return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
+}
 
 #ifdef RTI_CHECKED
 // Checked build: every array index is tested against the pitched allocation. The first
@@ -195,11 +201,15 @@ __device__ __forceinline__ float ring_none(float) { return __uint_as_float(0xfff
 __device__ __forceinline__ double ring_none(double) { return __longlong_as_double(-1LL); }
 
 // ------------------------------------------------------------------ momentum (R2-R4, R6)
+// First-order upwind difference on the sign of w (w = 0: the centred difference);
+// a difference that needs an unusable face is 0. Written as selects so that the
+// compiler can interleave the x and y updates.
 template <class T>
 __device__ __forceinline__ T upwind(T w, T phim, T phi0, T phip, bool okm, bool okp) {
-  if (w > T(0)) return okm ? phi0 - phim : T(0);
-  if (w < T(0)) return okp ? phip - phi0 : T(0);
-  return (okm && okp) ? T(0.5) * (phip - phim) : T(0);
+  const T pos = okm ? phi0 - phim : T(0);
+  const T neg = okp ? phip - phi0 : T(0);
+  const T mid = (okm && okp) ? T(0.5) * (phip - phim) : T(0);
+  return w > T(0) ? pos : (w < T(0) ? neg : mid);
 }
 
 // Arithmetic of the momentum update in the state precision. Binary64 keeps the oracle's
@@ -327,69 +337,51 @@ __device__ __forceinline__ bool lane_bit(unsigned mask, int lane, int d) {
 }
 
 // R2 + R4 at x-face (c, j): cells W = (c-1, j), E = (c, j); QX of faces c-1, c, c+1
-// and RX of rows j-1, j, j+1 with their usable flags.
+// and RX of rows j-1, j, j+1 with their usable flags. Every case of the wet/dry rule is
+// evaluated and the result selected (the values are those of the case analysis: a
+// discarded case may produce a NaN that is never selected).
 template <class T>
 __device__ __forceinline__ T xmom_r(T hL, T eL, T hR, T eR, T m, T nb, bool okm, T qm, T q0,
                                     bool okp, T qp, bool oks, T rs, T r0, bool okn, T rn,
                                     float nL, float nR, T eps, T dtdx, T g, T cfric, T dx,
                                     T q4dt) {
   const bool wL = hL + eL > eps, wR = hR + eR > eps;
-  T Df, grad, adv;
-  if (wL && wR) {
-    Df = T(0.5) * (hL + hR) + T(0.5) * (eL + eR);
-    grad = eR - eL;
-    const T ax = upwind(m, okm ? qm : T(0), q0, okp ? qp : T(0), okm, okp);
-    const T ay = upwind(nb, oks ? rs : T(0), r0, okn ? rn : T(0), oks, okn);
-    adv = dtdx * (ax + ay);
-  } else if (wL && !wR && eL > -hR) {
-    Df = eL + hR;
-    grad = -hR - eL;
-    adv = T(0);
-  } else if (wR && !wL && eR > -hL) {
-    Df = eR + hL;
-    grad = eR + hL;
-    adv = T(0);
-  } else {
-    return T(0);
-  }
-  if (!(Df > eps)) return T(0);
+  const bool both = wL && wR;
+  const bool oneL = wL && !wR && eL > -hR;  // water flows onto the dry east cell
+  const bool oneR = wR && !wL && eR > -hL;  // water flows onto the dry west cell
+  const T Df = both ? T(0.5) * (hL + hR) + T(0.5) * (eL + eR) : (oneL ? eL + hR : eR + hL);
+  const T grad = both ? eR - eL : (oneL ? -hR - eL : eR + hL);
+  const T ax = upwind(m, okm ? qm : T(0), q0, okp ? qp : T(0), okm, okp);
+  const T ay = upwind(nb, oks ? rs : T(0), r0, okn ? rn : T(0), oks, okn);
+  const T adv = both ? dtdx * (ax + ay) : T(0);
   const T nf = (T)(nL > nR ? nL : nR);
   const T m1 = Ar<T>::update(m, nb, Df, grad, adv, nf, g, dtdx, cfric);
-  if (!(wL && wR) && (wL ? m1 < T(0) : m1 > T(0))) return T(0);
-  return limit_outflow(m1, hL + eL, hR + eR, dx, q4dt);
+  const bool keep = (both || oneL || oneR) && Df > eps && (both || (wL ? !(m1 < T(0)) : !(m1 > T(0))));
+  const T lim = limit_outflow(m1, hL + eL, hR + eR, dx, q4dt);
+  return keep ? lim : T(0);
 }
 
 // R3 + R4 at y-face (c, j): cells S = (c, j-1), N = (c, j); SY of rows j-1, j, j+1 and
-// TY of faces c-1, c, c+1 with their usable flags.
+// TY of faces c-1, c, c+1 with their usable flags (selects as in xmom_r).
 template <class T>
 __device__ __forceinline__ T ymom_r(T hS, T eS, T hN, T eN, T v, T mb, bool okm, T sm, T s0,
                                     bool okp, T sp, bool okw, T tw, T t0, bool oke, T te,
                                     float nS, float nN, T eps, T dtdx, T g, T cfric, T dx,
                                     T q4dt) {
   const bool wS = hS + eS > eps, wN = hN + eN > eps;
-  T Df, grad, adv;
-  if (wS && wN) {
-    Df = T(0.5) * (hS + hN) + T(0.5) * (eS + eN);
-    grad = eN - eS;
-    const T ay = upwind(v, okm ? sm : T(0), s0, okp ? sp : T(0), okm, okp);
-    const T ax = upwind(mb, okw ? tw : T(0), t0, oke ? te : T(0), okw, oke);
-    adv = dtdx * (ay + ax);
-  } else if (wS && !wN && eS > -hN) {
-    Df = eS + hN;
-    grad = -hN - eS;
-    adv = T(0);
-  } else if (wN && !wS && eN > -hS) {
-    Df = eN + hS;
-    grad = eN + hS;
-    adv = T(0);
-  } else {
-    return T(0);
-  }
-  if (!(Df > eps)) return T(0);
+  const bool both = wS && wN;
+  const bool oneS = wS && !wN && eS > -hN;
+  const bool oneN = wN && !wS && eN > -hS;
+  const T Df = both ? T(0.5) * (hS + hN) + T(0.5) * (eS + eN) : (oneS ? eS + hN : eN + hS);
+  const T grad = both ? eN - eS : (oneS ? -hN - eS : eN + hS);
+  const T ay = upwind(v, okm ? sm : T(0), s0, okp ? sp : T(0), okm, okp);
+  const T ax = upwind(mb, okw ? tw : T(0), t0, oke ? te : T(0), okw, oke);
+  const T adv = both ? dtdx * (ay + ax) : T(0);
   const T nf = (T)(nS > nN ? nS : nN);
   const T v1 = Ar<T>::update(v, mb, Df, grad, adv, nf, g, dtdx, cfric);
-  if (!(wS && wN) && (wS ? v1 < T(0) : v1 > T(0))) return T(0);
-  return limit_outflow(v1, hS + eS, hN + eN, dx, q4dt);
+  const bool keep = (both || oneS || oneN) && Df > eps && (both || (wS ? !(v1 < T(0)) : !(v1 > T(0))));
+  const T lim = limit_outflow(v1, hS + eS, hN + eN, dx, q4dt);
+  return keep ? lim : T(0);
 }
 
 // R6: flux leaving through a root edge next to a cell (sign +1 east/north, -1 west/south)
@@ -399,13 +391,12 @@ __device__ __forceinline__ T radiate_r(T h, T e, T sign, T eps, T g) {
   return sign * (dsqrt(g * (h > T(0) ? h : T(0))) * e);
 }
 
-// Per-warp shared memory: the strip's block descriptor (and its parent's), the lanes'
-// binary64 budget partials (clip, outflow, ring) and the block index staged.
+// Per-warp shared memory: the strip's block descriptor (and its parent's), its
+// scenario counters and the index of the block staged.
 template <class T>
 struct WarpSlot {
   Blk<T> b;
   Blk<T> P;
-  double acc[3][32];
   ScenDev sc;
   int blk;
 };
@@ -539,13 +530,10 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   const bool col_x = c >= 1 && c <= nx - 1;  // x-face (c, .) is interior
   const bool col_y = c >= 0 && c <= nx - 1;  // y-face (c, .) lies on a cell column
   const int y0 = td.y0, ye = min(y0 + kp.ty, ny);
-  double& clip = ws.acc[0][lane];  // this lane's binary64 budget partials
-  double& outf = ws.acc[1][lane];
-  double& ring = ws.acc[2][lane];
-  clip = 0.0;
-  outf = 0.0;
-  ring = 0.0;
-  T vol_t = T(0);
+  // this lane's budget partials over the strip's rows (state precision, all branch-free
+  // adds; the strip's sums are formed and scaled in binary64 at the end)
+  T vol_t = T(0), clip_t = T(0), out_t = T(0), ring_t = T(0);
+  const bool edge_strip = td.x0 == 0 || td.x0 + kStripW >= nx || y0 == 0 || ye == ny;
   bool bad = false;
   size_t o = (size_t)(y0 - 2 + kYOff) * (size_t)pitch + (size_t)(c + kXOff);
 
@@ -573,13 +561,13 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     T e = cur.e - (dtdx * (Nw.mE - m) + dtdx * (nn - nS));
     const bool own = own_col && r >= y0 && r < ye;
     if (Nw.H + e < T(0)) {
-      if (own) clip += (double)(-Nw.H - e) * dx2;
+      clip_t += own ? -Nw.H - e : T(0);
       e = -Nw.H;
     }
     if (ring_strip) {  // fine-to-coarse override (R8), formed by the prepass
       const T rv = col_ok ? __ldcg(ringp + o) : ring_none(T(0));
       if (!ring_unset(rv) && col_y && r >= 0 && r < ny) {
-        if (own) ring += ((double)rv - (double)e) * dx2;
+        ring_t += own ? rv - e : T(0);
         e = rv;
       }
     }
@@ -593,10 +581,14 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
       }
       vol_t += e;
       bad |= !dfinite(e);
-      if (c == 0) outf += volc * (double)(-m);
-      if (c == nx - 1) outf += volc * (double)Nw.mE;
-      if (r == 0) outf += volc * (double)(-nS);
-      if (r == ny - 1) outf += volc * (double)nn;
+      if (edge_strip) {  // flux through the block's edges (outflow positive)
+        T of = T(0);
+        if (c == 0) of -= m;
+        if (c == nx - 1) of += Nw.mE;
+        if (r == 0) of -= nS;
+        if (r == ny - 1) of += nn;
+        out_t += of;
+      }
     }
 
     // ---- advective face terms of row r
@@ -635,18 +627,23 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     // ---- row j = r - 1: M^{n+1}, N^{n+1} (R2-R4) and the root edges (R6)
     if (r > y0) {
       const int j = r - 1;
-      const T qm = __shfl_up_sync(full, B.QX, 1), qp = __shfl_down_sync(full, B.QX, 1);
-      const T tw = __shfl_up_sync(full, B.TY, 1), te = __shfl_down_sync(full, B.TY, 1);
-      const float nmL = __shfl_up_sync(full, B.nm, 1);
-      const unsigned bx = __ballot_sync(full, B.vx), by = __ballot_sync(full, B.vy);
+      // a warp whose cells on both sides of every owned face are dry updates nothing
+      const bool act = own_col && (B.hL + B.eL > eps || B.H + B.E > eps || A.H + A.E > eps);
+      T xm = T(0), ym = T(0);
+      if (__any_sync(full, act)) {
+        const T qm = __shfl_up_sync(full, B.QX, 1), qp = __shfl_down_sync(full, B.QX, 1);
+        const T tw = __shfl_up_sync(full, B.TY, 1), te = __shfl_down_sync(full, B.TY, 1);
+        const float nmL = __shfl_up_sync(full, B.nm, 1);
+        const unsigned bx = __ballot_sync(full, B.vx), by = __ballot_sync(full, B.vy);
+        xm = xmom_r(B.hL, B.eL, B.H, B.E, B.MX, B.nb, lane_bit(bx, lane, -1), qm, B.QX,
+                    lane_bit(bx, lane, 1), qp, A.vx, A.RX, B.RX, C.vx, C.RX, nmL, B.nm, eps,
+                    dtdx, g, cfric, dx, q4dt);
+        ym = ymom_r(A.H, A.E, B.H, B.E, B.NY, B.mb, A.vy, A.SY, B.SY, C.vy, C.SY,
+                    lane_bit(by, lane, -1), tw, B.TY, lane_bit(by, lane, 1), te, A.nm, B.nm,
+                    eps, dtdx, g, cfric, dx, q4dt);
+      }
       if (own_col) {
         const size_t oj = o - (size_t)pitch;
-        const T xm = xmom_r(B.hL, B.eL, B.H, B.E, B.MX, B.nb, lane_bit(bx, lane, -1), qm, B.QX,
-                            lane_bit(bx, lane, 1), qp, A.vx, A.RX, B.RX, C.vx, C.RX, nmL, B.nm,
-                            eps, dtdx, g, cfric, dx, q4dt);
-        const T ym = ymom_r(A.H, A.E, B.H, B.E, B.NY, B.mb, A.vy, A.SY, B.SY, C.vy, C.SY,
-                            lane_bit(by, lane, -1), tw, B.TY, lane_bit(by, lane, 1), te, A.nm,
-                            B.nm, eps, dtdx, g, cfric, dx, q4dt);
         if (c >= 1) Mq[oj] = xm;
         else if (root) Mq[oj] = bcW == kBcRadiation ? radiate_r(B.H, B.E, T(-1), eps, g) : T(0);
         if (c == nx - 1 && root)
@@ -662,7 +659,8 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   // ---- the strip's budget partials (binary64, fixed reduction order)
   if (bad) atomicOr(b.status, kStNonFinite);
   const double vs = warp_sum((double)vol_t);
-  const double cs = warp_sum(clip), os = warp_sum(outf), rs = warp_sum(ring);
+  const double cs = warp_sum((double)clip_t) * dx2, os = warp_sum((double)out_t) * volc,
+               rs = warp_sum((double)ring_t) * dx2;
   if (lane == 0) {
     double* slot = b.budget + 4 * (size_t)((y0 / kp.ty) * b.tiles_x + td.x0 / kp.tx);
     slot[0] = vs;
