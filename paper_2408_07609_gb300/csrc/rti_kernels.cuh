@@ -216,12 +216,29 @@ __device__ __forceinline__ T upwind(T w, T phim, T phi0, T phip, bool okm, bool 
 // exact expressions (correctly rounded divide and square root, library cbrt) so that it
 // reproduces the oracle's rounding. Binary32 (the forecast path, checked against the
 // oracle within the stated accuracy) uses the special-function unit: approximate
-// reciprocal, reciprocal square root, and D^(-7/3) = exp(-7/3 ln D).
+// reciprocals, and sqrt(M^2 + N^2) D^(-7/3) = 2^(log2(M^2 + N^2)/2 - 7/3 log2 D) with
+// the PTX lg2.approx / ex2.approx instructions (log2 0 = -inf gives a zero friction).
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <class T>
 struct Ar;
 template <>
 struct Ar<double> {
-  static __device__ __forceinline__ double quot(double a, double b) { return a / b; }
+  static constexpr bool kSelect = false;  // divide only where the quotient is used
+  static __device__ __forceinline__ void quot2(double a1, double a2, double b, double& q1,
+                                               double& q2) {
+    q1 = a1 / b;
+    q2 = a2 / b;
+  }
   static __device__ __forceinline__ double update(double m, double across, double Df,
                                                   double grad, double adv, double nf,
                                                   double g, double dtdx, double cfric) {
@@ -232,15 +249,20 @@ struct Ar<double> {
 };
 template <>
 struct Ar<float> {
-  static __device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
+  static constexpr bool kSelect = true;  // divide everywhere and select (no branch)
+  static __device__ __forceinline__ void quot2(float a1, float a2, float b, float& q1,
+                                               float& q2) {
+    const float r = __fdividef(1.0f, b);
+    q1 = a1 * r;
+    q2 = a2 * r;
+  }
   static __device__ __forceinline__ float update(float m, float across, float Df, float grad,
                                                  float adv, float nf, float g, float dtdx,
                                                  float cfric) {
-    const float P = g * Df * dtdx * grad;
+    const float P = (g * dtdx) * Df * grad;
     const float s2 = m * m + across * across;
-    const float sq = s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f;
-    const float d73inv = __expf(-2.33333333f * __logf(Df));
-    const float F = cfric * nf * nf * sq * d73inv;
+    const float F =
+        (cfric * nf * nf) * ex2_approx(0.5f * lg2_approx(s2) - 2.33333333f * lg2_approx(Df));
     return __fdividef((1.0f - F) * m - adv - P, 1.0f + F);
   }
 };
@@ -508,19 +530,15 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   const bool root = !b.is_child;
   const T dtdx = b.dtdx, eps = b.eps, g = b.g, cfric = b.cfric, dx = b.dx, q4dt = b.q4dt;
   const T thr = b.thr;
-  const double volc = b.vol, dx2 = b.dx2;
-  const int bcW = b.bc[0], bcE = b.bc[1], bcS = b.bc[2], bcN = b.bc[3];
   const T* etaP = b.eta[p];
   const T* Mp = b.M[p];
   const T* Np = b.N[p];
   const T* hh = b.h;
   const float* man = b.man;
-  const T* ringp = b.ring;
   T* etaQ = b.eta[q];
   T* Mq = b.M[q];
   T* Nq = b.N[q];
   T* emax = b.emax;
-  int* arr = b.arr;
   const bool ring_strip = (td.flags & kTfRing) != 0;
   const unsigned full = 0xffffffffu;
 
@@ -529,8 +547,9 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   const bool own_col = lane >= 2 && lane < 2 + kStripW && c < nx;
   const bool col_x = c >= 1 && c <= nx - 1;  // x-face (c, .) is interior
   const bool col_y = c >= 0 && c <= nx - 1;  // y-face (c, .) lies on a cell column
+  const int sl = (lane - 1) & 31, sr = (lane + 1) & 31;  // neighbour bit of a ballot
   const int y0 = td.y0, ye = min(y0 + kp.ty, ny);
-  // this lane's budget partials over the strip's rows (state precision, all branch-free
+  // this lane's budget partials over the strip's rows (state precision, branch-free
   // adds; the strip's sums are formed and scaled in binary64 at the end)
   T vol_t = T(0), clip_t = T(0), out_t = T(0), ring_t = T(0);
   const bool edge_strip = td.x0 == 0 || td.x0 + kStripW >= nx || y0 == 0 || ye == ny;
@@ -542,12 +561,11 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   T nSL = __shfl_up_sync(full, nS, 1);
   Raw<T> R0 = load_raw(etaP, hh, Mp, Np, emax, man, o, pitch, col_ok);
   Raw<T> R1 = load_raw(etaP, hh, Mp, Np, emax, man, o + pitch, pitch, col_ok);
-  Row<T> A = {}, B = {}, C = {};  // rows r-2, r-1, r once row r is formed
+  Row<T> A = {}, B = {}, C = {};
 
-  for (int r = y0 - 2; r <= ye; ++r, o += pitch) {
-    const Raw<T> cur = R0;
-    R0 = R1;
-    if (r + 2 <= ye) R1 = load_raw(etaP, hh, Mp, Np, emax, man, o + 2 * (size_t)pitch, pitch, col_ok);
+  // One row r from its inputs `cur`: X receives row r; Y, Z are rows r - 2, r - 1.
+  auto row = [&](const Raw<T>& cur, Row<T>& X, const Row<T>& Y, const Row<T>& Z, int r) {
+    const bool rin_x = r >= 0 && r <= ny - 1, rin_y = r >= 1 && r <= ny - 1;
 
     // ---- row r: eta^{n+1} (R1, R5, R7 pulls, R8 ring) and the output update (R9)
     Row<T> Nw;
@@ -565,8 +583,8 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
       e = -Nw.H;
     }
     if (ring_strip) {  // fine-to-coarse override (R8), formed by the prepass
-      const T rv = col_ok ? __ldcg(ringp + o) : ring_none(T(0));
-      if (!ring_unset(rv) && col_y && r >= 0 && r < ny) {
+      const T rv = col_ok ? __ldcg(b.ring + o) : ring_none(T(0));
+      if (!ring_unset(rv) && col_y && rin_x) {
         ring_t += own ? rv - e : T(0);
         e = rv;
       }
@@ -576,7 +594,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
       etaQ[o] = e;
       const T em = cur.em;
       if (Nw.H + e > eps && e > em) {
-        if (em < thr && e >= thr) arr[o] = sn;
+        if (em < thr && e >= thr) b.arr[o] = sn;
         emax[o] = e;
       }
       vol_t += e;
@@ -596,71 +614,79 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     Nw.hL = __shfl_up_sync(full, Nw.H, 1);
     {  // x-face (c, r)
       const T dep = T(0.5) * (Nw.hL + Nw.H) + T(0.5) * (Nw.eL + Nw.E);
-      const bool in = col_x && r >= 0 && r <= ny - 1;
+      const bool in = col_x && rin_x;
       Nw.vx = in && dep > eps;
       Nw.nb = T(0.25) * ((nSL + nS) + (nnL + nn));
-      Nw.QX = T(0);
-      Nw.RX = T(0);
-      if (in && dep != T(0)) {
-        Nw.QX = Ar<T>::quot(m * m, dep);
-        Nw.RX = Ar<T>::quot(m * Nw.nb, dep);
-      }
+      T qx = T(0), rx = T(0);
+      const bool use = in && dep != T(0);
+      if (Ar<T>::kSelect || use) Ar<T>::quot2(m * m, m * Nw.nb, dep, qx, rx);
+      Nw.QX = use ? qx : T(0);
+      Nw.RX = use ? rx : T(0);
     }
     {  // y-face (c, r)
-      const T dep = T(0.5) * (C.H + Nw.H) + T(0.5) * (C.E + Nw.E);
-      const bool in = col_y && r >= 1 && r <= ny - 1;
+      const T dep = T(0.5) * (Z.H + Nw.H) + T(0.5) * (Z.E + Nw.E);
+      const bool in = col_y && rin_y;
       Nw.vy = in && dep > eps;
-      Nw.mb = T(0.25) * ((C.MX + m) + (C.mE + Nw.mE));
-      Nw.SY = T(0);
-      Nw.TY = T(0);
-      if (in && dep != T(0)) {
-        Nw.SY = Ar<T>::quot(nS * nS, dep);
-        Nw.TY = Ar<T>::quot(nS * Nw.mb, dep);
-      }
+      Nw.mb = T(0.25) * ((Z.MX + m) + (Z.mE + Nw.mE));
+      T sy = T(0), ty = T(0);
+      const bool use = in && dep != T(0);
+      if (Ar<T>::kSelect || use) Ar<T>::quot2(nS * nS, nS * Nw.mb, dep, sy, ty);
+      Nw.SY = use ? sy : T(0);
+      Nw.TY = use ? ty : T(0);
     }
-    A = B;
-    B = C;
-    C = Nw;
+    X = Nw;
     nS = nn;
     nSL = nnL;
 
-    // ---- row j = r - 1: M^{n+1}, N^{n+1} (R2-R4) and the root edges (R6)
+    // ---- row j = r - 1 (rows Y, Z, X = j-1, j, j+1): M^{n+1}, N^{n+1} (R2-R4), root edges (R6)
     if (r > y0) {
       const int j = r - 1;
       // a warp whose cells on both sides of every owned face are dry updates nothing
-      const bool act = own_col && (B.hL + B.eL > eps || B.H + B.E > eps || A.H + A.E > eps);
+      const bool act = own_col && (Z.hL + Z.eL > eps || Z.H + Z.E > eps || Y.H + Y.E > eps);
       T xm = T(0), ym = T(0);
       if (__any_sync(full, act)) {
-        const T qm = __shfl_up_sync(full, B.QX, 1), qp = __shfl_down_sync(full, B.QX, 1);
-        const T tw = __shfl_up_sync(full, B.TY, 1), te = __shfl_down_sync(full, B.TY, 1);
-        const float nmL = __shfl_up_sync(full, B.nm, 1);
-        const unsigned bx = __ballot_sync(full, B.vx), by = __ballot_sync(full, B.vy);
-        xm = xmom_r(B.hL, B.eL, B.H, B.E, B.MX, B.nb, lane_bit(bx, lane, -1), qm, B.QX,
-                    lane_bit(bx, lane, 1), qp, A.vx, A.RX, B.RX, C.vx, C.RX, nmL, B.nm, eps,
+        const T qm = __shfl_up_sync(full, Z.QX, 1), qp = __shfl_down_sync(full, Z.QX, 1);
+        const T tw = __shfl_up_sync(full, Z.TY, 1), te = __shfl_down_sync(full, Z.TY, 1);
+        const float nmL = __shfl_up_sync(full, Z.nm, 1);
+        const unsigned bx = __ballot_sync(full, Z.vx), by = __ballot_sync(full, Z.vy);
+        xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, ((bx >> sl) & 1u) != 0, qm, Z.QX,
+                    ((bx >> sr) & 1u) != 0, qp, Y.vx, Y.RX, Z.RX, X.vx, X.RX, nmL, Z.nm, eps,
                     dtdx, g, cfric, dx, q4dt);
-        ym = ymom_r(A.H, A.E, B.H, B.E, B.NY, B.mb, A.vy, A.SY, B.SY, C.vy, C.SY,
-                    lane_bit(by, lane, -1), tw, B.TY, lane_bit(by, lane, 1), te, A.nm, B.nm,
+        ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.vy, Y.SY, Z.SY, X.vy, X.SY,
+                    ((by >> sl) & 1u) != 0, tw, Z.TY, ((by >> sr) & 1u) != 0, te, Y.nm, Z.nm,
                     eps, dtdx, g, cfric, dx, q4dt);
       }
       if (own_col) {
         const size_t oj = o - (size_t)pitch;
         if (c >= 1) Mq[oj] = xm;
-        else if (root) Mq[oj] = bcW == kBcRadiation ? radiate_r(B.H, B.E, T(-1), eps, g) : T(0);
+        else if (root) Mq[oj] = b.bc[0] == kBcRadiation ? radiate_r(Z.H, Z.E, T(-1), eps, g) : T(0);
         if (c == nx - 1 && root)
-          Mq[oj + 1] = bcE == kBcRadiation ? radiate_r(B.H, B.E, T(1), eps, g) : T(0);
+          Mq[oj + 1] = b.bc[1] == kBcRadiation ? radiate_r(Z.H, Z.E, T(1), eps, g) : T(0);
         if (j >= 1) Nq[oj] = ym;
-        else if (root) Nq[oj] = bcS == kBcRadiation ? radiate_r(B.H, B.E, T(-1), eps, g) : T(0);
+        else if (root) Nq[oj] = b.bc[2] == kBcRadiation ? radiate_r(Z.H, Z.E, T(-1), eps, g) : T(0);
         if (j == ny - 1 && root)
-          Nq[oj + pitch] = bcN == kBcRadiation ? radiate_r(B.H, B.E, T(1), eps, g) : T(0);
+          Nq[oj + pitch] = b.bc[3] == kBcRadiation ? radiate_r(Z.H, Z.E, T(1), eps, g) : T(0);
       }
     }
+    o += pitch;
+  };
+
+  for (int r = y0 - 2; r <= ye; ++r) {
+    const Raw<T> cur = R0;
+    R0 = R1;
+    if (r + 2 <= ye) R1 = load_raw(etaP, hh, Mp, Np, emax, man, o + 2 * (size_t)pitch, pitch, col_ok);
+    Row<T> X;
+    row(cur, X, B, C, r);
+    A = B;  // rows r-2, r-1, r
+    B = C;
+    C = X;
   }
 
   // ---- the strip's budget partials (binary64, fixed reduction order)
   if (bad) atomicOr(b.status, kStNonFinite);
   const double vs = warp_sum((double)vol_t);
-  const double cs = warp_sum((double)clip_t) * dx2, os = warp_sum((double)out_t) * volc,
-               rs = warp_sum((double)ring_t) * dx2;
+  const double cs = warp_sum((double)clip_t) * b.dx2, os = warp_sum((double)out_t) * b.vol,
+               rs = warp_sum((double)ring_t) * b.dx2;
   if (lane == 0) {
     double* slot = b.budget + 4 * (size_t)((y0 / kp.ty) * b.tiles_x + td.x0 / kp.tx);
     slot[0] = vs;
