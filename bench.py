@@ -44,11 +44,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--fp64-steps", type=int, default=20)
-    ap.add_argument("--schedule", type=int, default=0, help="0 persistent, 1 two launches/step")
+    ap.add_argument("--schedule", type=int, default=0, help="0 persistent, 1 one launch per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--tile", type=int, nargs=2, default=(0, 0), help="tile shape (0 0 = default)")
+    ap.add_argument("--tile", type=int, nargs=2, default=(0, 0), help="strip shape (0 0 = default)")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-n", type=int, default=30, help="requests in the serving trace")
+    ap.add_argument("--serve-scale", type=float, default=1.0 / 60.0,
+                    help="time scale of the serving trace (arrivals and durations)")
+    ap.add_argument("--serve-pool-gb", type=int, default=32)
+    ap.add_argument("--no-accuracy", action="store_true")
     return ap.parse_args()
 
 
@@ -204,6 +210,98 @@ def time_e2e(rti, sc, steps, world):
     return wall, h2d, d2h
 
 
+def serving(rti, sc5, a, world):
+    """Continuous-batching FP32 serving of a Poisson trace (mean inter-arrival 20 s, kinds
+    3-/4-/5-level uniform, 1-6 simulated hours), time-scaled by --serve-scale, beside the
+    plain per-scenario FP64 path (one request at a time, no batching) timed on a sample of
+    the same requests and applied to the trace's work."""
+    import torch
+
+    from paper_2408_07609_gb300 import scenarios as S
+    from paper_2408_07609_gb300 import serve
+
+    sites = {"3level": S.serving_hierarchy("3level", seed=1000, hours=0.0),
+             "4level": S.serving_hierarchy("4level", seed=1001, hours=0.0), "5level": sc5}
+    trace = S.poisson_trace(seed=2024, n=a.serve_n, mean_s=20.0)
+    barrier(world)
+    srv = serve.Server(sites, pool_bytes=a.serve_pool_gb << 30, precision=rti.FP32,
+                       chunk_steps=50)
+    reqs, st = srv.run(trace, time_scale=a.serve_scale, max_wall_s=180.0)
+    srv.close()
+    del srv
+    torch.cuda.empty_cache()
+    # plain FP64 path: each request alone, create .. results on host, one after another;
+    # timed on the smallest request of each kind, applied per kind to the trace's work
+    per_kind = {}
+    for r in sorted(reqs, key=lambda r: r.cells * r.nsteps):
+        if r.kind in per_kind:
+            continue
+        sc = S.with_new_source(sites[r.kind], r.seed)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = rti.Handle.from_scenario(sc, precision=rti.FP64)
+        h.step(r.nsteps)
+        for k in range(len(sc.blocks)):
+            h.max_height(k)
+            h.arrival_time(k)
+        h.close()
+        per_kind[r.kind] = (time.perf_counter() - t0) / (r.cells * r.nsteps)
+    service64 = sum(r.cells * r.nsteps * per_kind[r.kind] for r in reqs)
+    return {"scenarios_per_h": st["scenarios_per_h"], "p50_s": st["p50_s"], "p99_s": st["p99_s"],
+            "mean_s": st["mean_s"], "completed": st["completed"], "requests": st["requests"],
+            "max_live": st["max_live"], "gcups": st["gcups"], "precision": "fp32",
+            "trace": f"{a.serve_n} Poisson arrivals (mean 20 s), 3/4/5-level uniform, "
+                     f"1-6 h; arrivals and durations x{a.serve_scale:.4g}; "
+                     f"HBM pool {a.serve_pool_gb} GB; chunk 50 steps",
+            "fp64_plain": {"scenarios_per_h": len(reqs) / service64 * 3600.0,
+                           "gcups_by_kind": {k: 1e-9 / v for k, v in per_kind.items()},
+                           "how": "the smallest request of each kind alone in FP64 (create, "
+                                  "uplift, steps, results to host), one after another; its "
+                                  "time per cell-step applied to every request of that kind"}}
+
+
+def accuracy(rti):
+    """FP32 against the FP64 path (which matches the FP64 oracle to 1e-12) on the 3-level
+    C2 nest over its full hour: max |eta| and max-height error (m), wet/dry mismatch (%
+    of cells, final state and ever-wet), arrival-time error (s)."""
+    import numpy as np
+
+    from paper_2408_07609_gb300 import scenarios as S
+
+    sc = S.config2()
+    out = {}
+    hs = {p: rti.Handle.from_scenario(sc, precision=p) for p in (rti.FP32, rti.FP64)}
+    for h in hs.values():
+        h.step(sc.steps)
+    e_eta = e_max = 0.0
+    mis_wet = mis_ever = n = 0
+    arr_err, arr_mis = [], 0
+    for k, b in enumerate(sc.blocks):
+        h0 = np.asarray(sc.bathy[k])
+        e32, e64 = hs[rti.FP32].get_state(k)[0], hs[rti.FP64].get_state(k)[0]
+        m32, m64 = hs[rti.FP32].max_height(k), hs[rti.FP64].max_height(k)
+        a32, a64 = hs[rti.FP32].arrival_time(k), hs[rti.FP64].arrival_time(k)
+        e_eta = max(e_eta, float(np.abs(e32 - e64).max()))
+        both = ~np.isnan(m32) & ~np.isnan(m64)
+        if both.any():
+            e_max = max(e_max, float(np.abs(m32[both] - m64[both]).max()))
+        mis_wet += int(((h0 + e32 > sc.dry_eps) != (h0 + e64 > sc.dry_eps)).sum())
+        mis_ever += int((np.isnan(m32) != np.isnan(m64)).sum())
+        n += h0.size
+        ab = (a32 >= 0) & (a64 >= 0)
+        arr_err.append(np.abs(a32[ab] - a64[ab]))
+        arr_mis += int(((a32 >= 0) != (a64 >= 0)).sum())
+    for h in hs.values():
+        h.close()
+    ae = np.concatenate(arr_err)
+    return {"workload": sc.name, "against": "FP64 GPU path", "steps": sc.steps,
+            "max_abs_eta_m": e_eta, "max_abs_max_height_m": e_max,
+            "wet_dry_mismatch_pct": 100.0 * mis_wet / n, "ever_wet_mismatch_pct": 100.0 * mis_ever / n,
+            "arrival_max_err_s": float(ae.max()) if ae.size else 0.0,
+            "arrival_mean_err_s": float(ae.mean()) if ae.size else 0.0,
+            "arrival_mismatch_cells": arr_mis}
+
+
 def cpu_baseline(sc, steps):
     """The FP64 oracle, as it stands, on the host: a bounded sample of the workload."""
     from oracle import oracle
@@ -226,6 +324,7 @@ def run_ours(a):
     build.build()
     sc = workload()
     cells = sc.cells
+    fp32_bytes = rti.footprint(sc.blocks, rti.make_params(sc.dt, precision=rti.FP32))
     with Clocks(local) as clk:
         ms32 = time_device(rti, sc, rti.FP32, a.steps, a.warmup, a.schedule, world, a.tile)
     clocks = clk.summary()
@@ -247,6 +346,8 @@ def run_ours(a):
                "h2d_bytes_per_step": h2d // a.steps, "d2h_bytes_per_step": d2h // a.steps,
                "includes": "create (bathymetry, Manning n), initial uplift, steps, max depth "
                            "and arrival of every block read back"}
+    srv = None if a.no_serving else serving(rti, sc, a, world)
+    acc = None if (a.no_accuracy or rank != 0) else accuracy(rti)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         dt = cpu_baseline(sc, a.cpu_steps)
@@ -263,9 +364,9 @@ def run_ours(a):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": sc.name, "cells": cells, "blocks": len(sc.blocks),
                        "levels": 5, "dt_s": sc.dt, "precision": "fp32",
-                       "schedule": "persistent" if a.schedule == 0 else "two launches/step",
-                       "tile": list(a.tile) if a.tile[0] else [64, 16],
-                       "l2": "working set 1.9 GB (fp32) > 129 MB L2; no flush",
+                       "schedule": "persistent" if a.schedule == 0 else "one launch per step",
+                       "strip": list(a.tile) if a.tile[0] else [28, 64],
+                       "l2": f"working set {fp32_bytes / 1e9:.2f} GB (fp32) > 129 MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "fp64": {"value": gcups64, "unit": "GCUPS", "ms_per_step": per64,
                      "steps": a.fp64_steps},
@@ -274,7 +375,9 @@ def run_ours(a):
                           "paper_context": "Kochi 47.2 M cells: 82 s on 32 H100 PCIe, "
                                            "< 2.5 min on 32 Sapphire Rapids CPUs"},
             "e2e": e2e,
-            "gpu_launches": 3,
+            "gpu_launches": 3 if a.schedule == 0 else a.steps + 2,
+            "serving": srv,
+            "fp32_accuracy": acc,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_kind": f"{kind} hbm_gbs",

@@ -209,7 +209,42 @@ def coastal_hierarchy(name, seed, root, levels, dt, steps, *, deep=4000.0, trenc
     clean = [{k: v for k, v in b.items() if k in ("level", "parent", "nx", "ny", "i0", "j0", "dx",
                                                    "bc")} for b in blocks]
     return Scenario(name=name, blocks=clean, bathy=bathy, manning=manning, uplift=uplift, dt=dt,
-                    steps=steps, meta=dict(seed=seed, source=(xs, ys)))
+                    steps=steps, meta=dict(seed=seed, source=(xs, ys), margin=mg,
+                                           origin=[(b["x0"], b["y0"]) for b in blocks],
+                                           source_shape=source, extent=(Lx, Ly),
+                                           shelf=(shelf_w, slope_w)))
+
+
+def with_new_source(site: Scenario, seed: int, peak_range=(2.0, 6.0)) -> Scenario:
+    """The same grids, bathymetry and Manning n as `site`, with a new seeded offshore
+    source of the site's shape (position along the coast, distance offshore, strike and
+    peak drawn from `seed`). Only blocks that the source touches get an uplift array."""
+    rng = np.random.default_rng(seed)
+    mg, (Lx, Ly) = site.meta["margin"], site.meta["extent"]
+    shelf_w, slope_w = site.meta["shelf"]
+    shape = dict(site.meta["source_shape"] or dict(kind="ellipse", a=50e3, b=25e3, peak=3.0))
+    shape["peak"] = float(rng.uniform(*peak_range))
+    ys = Ly * rng.uniform(0.3, 0.7)
+    xs = mg.xc(np.array([ys]))[0] - (shelf_w + slope_w * rng.uniform(0.6, 1.2))
+    theta = 0.5 * math.pi + rng.uniform(-0.25, 0.25)
+    reach = max(shape.get("a", 0.0), 3.0 * shape.get("sigma", 0.0))
+    uplift = []
+    for b, (x0, y0) in zip(site.blocks, site.meta["origin"]):
+        w, h = b["nx"] * b["dx"], b["ny"] * b["dx"]
+        if x0 > xs + reach or x0 + w < xs - reach or y0 > ys + reach or y0 + h < ys - reach:
+            uplift.append(None)
+            continue
+        x = x0 + (np.arange(b["nx"]) + 0.5) * b["dx"]
+        y = y0 + (np.arange(b["ny"]) + 0.5) * b["dx"]
+        if shape["kind"] == "ellipse":
+            f = _ellipse_uplift(x, y, xs, ys, shape["a"], shape["b"], theta, shape["peak"])
+        else:
+            f = _gauss_uplift(x, y, xs, ys, shape["sigma"], shape["peak"])
+        uplift.append(f if np.any(f != 0) else None)
+    meta = dict(site.meta, seed=seed, source=(xs, ys))
+    return Scenario(name=f"{site.name} / source {seed}", blocks=site.blocks, bathy=site.bathy,
+                    manning=site.manning, uplift=uplift, dt=site.dt, steps=site.steps,
+                    g=site.g, dry_eps=site.dry_eps, arrival_thr=site.arrival_thr, meta=meta)
 
 
 # --------------------------------------------------------------------------- workloads

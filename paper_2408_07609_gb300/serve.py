@@ -1,0 +1,204 @@
+"""Continuous-batching forecast server over the batch API.
+
+Requests (an earthquake source on one of a few pre-built grid hierarchies, the "sites")
+arrive over time. A request is admitted as soon as it has arrived and its device
+footprint (rti_footprint) fits in a fixed HBM pool; its state then stays resident in the
+pool while the batch steps it together with every other live request, chunk by chunk,
+in one graph-captured persistent launch. Requests that finish leave the batch between
+chunks, their results (maximum height and arrival time of every block) are read back to
+the host, and their memory returns to the pool, so new arrivals join while others run.
+Time to forecast is measured from a request's arrival to the moment its results are on
+the host.
+
+The pool is one caller-owned device allocation (a torch uint8 tensor) carved first-fit
+into 256-byte aligned arenas, so admission and retirement allocate nothing on the
+device and never stall the running batch.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import rti
+from . import scenarios as S
+
+ALIGN = 256
+
+
+class Pool:
+    """First-fit allocator of 256-byte aligned ranges of one device buffer."""
+
+    def __init__(self, nbytes: int, device_buffer=None):
+        self.size = int(nbytes) // ALIGN * ALIGN
+        self.buf = device_buffer
+        self.free = [(0, self.size)]  # sorted (offset, length)
+        self.used = {}
+
+    def alloc(self, nbytes: int):
+        need = (int(nbytes) + ALIGN - 1) // ALIGN * ALIGN
+        for k, (off, ln) in enumerate(self.free):
+            if ln >= need:
+                if ln == need:
+                    self.free.pop(k)
+                else:
+                    self.free[k] = (off + need, ln - need)
+                self.used[off] = need
+                return off
+        return None
+
+    def release(self, off: int):
+        ln = self.used.pop(off)
+        self.free.append((off, ln))
+        self.free.sort()
+        merged = []
+        for o, n in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == o:
+                merged[-1] = (merged[-1][0], merged[-1][1] + n)
+            else:
+                merged.append((o, n))
+        self.free = merged
+
+    def view(self, off: int):
+        return self.buf[off:off + self.used[off]]
+
+    @property
+    def in_use(self) -> int:
+        return sum(self.used.values())
+
+
+@dataclass
+class Request:
+    rid: int
+    kind: str
+    seed: int
+    hours: float
+    arrival_s: float
+    nsteps: int = 0
+    footprint: int = 0
+    cells: int = 0
+    admitted_s: float = float("nan")
+    done_s: float = float("nan")
+    result: dict = field(default_factory=dict)
+
+    @property
+    def latency_s(self) -> float:
+        return self.done_s - self.arrival_s
+
+
+def load_sites(kinds=("3level", "4level", "5level"), seed=1000):
+    """One fixed hierarchy per kind (the site's grids; requests only change the source)."""
+    return {k: S.serving_hierarchy(k, seed=seed + i, hours=0.0) for i, k in enumerate(kinds)}
+
+
+class Server:
+    def __init__(self, sites: dict, pool_bytes: int, precision=rti.FP32, chunk_steps: int = 50,
+                 schedule=rti.SCHED_PERSISTENT, keep_fields: bool = False):
+        import torch
+
+        self.torch = torch
+        self.sites = sites
+        self.prec = precision
+        self.keep = keep_fields
+        self.pool = Pool(pool_bytes, torch.empty(int(pool_bytes), dtype=torch.uint8,
+                                                 device="cuda"))
+        self.batch = rti.Batch(precision, schedule, chunk_steps)
+        self.stream = torch.cuda.Stream()
+        self.chunk = chunk_steps
+
+    def _admit(self, req: Request, live: dict):
+        site = self.sites[req.kind]
+        sc = S.with_new_source(site, req.seed)
+        off = self.pool.alloc(req.footprint)
+        if off is None:
+            return False
+        h = rti.Handle.from_scenario(sc, precision=self.prec, device_mem=self.pool.view(off))
+        self.batch.add(h, req.nsteps)
+        live[req.rid] = (req, h, off)
+        return True
+
+    def _retire(self, req: Request, h: rti.Handle, off: int, t0: float):
+        out = {}
+        for k in range(len(h.blocks)):
+            mh, at = h.max_height(k), h.arrival_time(k)
+            if self.keep:
+                out[k] = (mh, at)
+            else:
+                wet = ~np.isnan(mh)
+                out[k] = (float(np.nanmax(mh)) if wet.any() else float("nan"),
+                          int((at >= 0).sum()))
+        req.result = out
+        req.done_s = time.perf_counter() - t0
+        self.batch.remove(h)
+        h.close()
+        self.pool.release(off)
+
+    def run(self, trace, time_scale: float = 1.0, max_wall_s: float | None = None,
+            admit_per_chunk: int | None = None):
+        """Serve `trace` (dicts with arrival_s, kind, seed, hours); arrival times and
+        simulated durations are multiplied by time_scale. At most admit_per_chunk
+        requests join between two chunks (None: all that have arrived and fit).
+        Returns (requests, stats)."""
+        reqs = []
+        for i, t in enumerate(trace):
+            site = self.sites[t["kind"]]
+            nsteps = max(1, int(round(t["hours"] * 3600.0 * time_scale / site.dt)))
+            r = Request(i, t["kind"], int(t["seed"]), float(t["hours"]),
+                        float(t["arrival_s"]) * time_scale, nsteps)
+            p = rti.make_params(site.dt, site.g, site.dry_eps, site.arrival_thr, self.prec)
+            r.footprint = rti.footprint(site.blocks, p)
+            r.cells = site.cells
+            if r.footprint > self.pool.size:
+                raise ValueError(f"request {i} ({r.kind}) needs {r.footprint} B, pool is {self.pool.size}")
+            reqs.append(r)
+        pending = list(reqs)
+        live = {}
+        max_live, chunks = 0, 0
+        t0 = time.perf_counter()
+        while pending or live:
+            now = time.perf_counter() - t0
+            if max_wall_s is not None and now > max_wall_s:
+                break
+            launched = False
+            if live:
+                with self.torch.cuda.stream(self.stream):
+                    self.batch.step(self.stream)
+                launched = True
+                chunks += 1
+            # admissions overlap the chunk in flight (arrival order, while memory fits)
+            admitted = 0
+            while pending and pending[0].arrival_s <= time.perf_counter() - t0:
+                if admit_per_chunk is not None and admitted >= admit_per_chunk:
+                    break
+                r = pending[0]
+                if not self._admit(r, live):
+                    break
+                r.admitted_s = time.perf_counter() - t0
+                pending.pop(0)
+                admitted += 1
+            max_live = max(max_live, len(live))
+            if launched:
+                self.batch.sync()
+                for rid in [k for k, (r, h, o) in live.items() if self.batch.remaining(h) == 0]:
+                    r, h, off = live.pop(rid)
+                    self._retire(r, h, off, t0)
+            elif pending and not live:
+                time.sleep(max(0.0, min(0.05, pending[0].arrival_s - (time.perf_counter() - t0))))
+        wall = time.perf_counter() - t0
+        done = [r for r in reqs if np.isfinite(r.done_s)]
+        lat = np.array([r.latency_s for r in done]) if done else np.array([float("nan")])
+        cell_steps = float(sum(r.cells * r.nsteps for r in done))
+        stats = dict(requests=len(reqs), completed=len(done), wall_s=wall,
+                     scenarios_per_h=len(done) / wall * 3600.0 if wall > 0 else float("nan"),
+                     p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+                     mean_s=float(lat.mean()), max_live=max_live, chunks=chunks,
+                     gcups=cell_steps / wall / 1e9 if wall > 0 else float("nan"),
+                     time_scale=time_scale)
+        return reqs, stats
+
+    def close(self):
+        for h in list(self.batch.members):
+            self.batch.remove(h)
+            h.close()
+        self.batch.close()

@@ -1,0 +1,78 @@
+"""Accuracy of the binary32 path against the binary64 oracle (forecast outputs).
+
+The FP32 forecast path stores eta as the deviation from still water and computes
+fluxes in binary32 with approximate special functions, so it does not round like the
+oracle; it is held to forecast-level bounds instead of parity:
+
+  max |eta error| and max |max-height error|  <= 5 cm
+  wet/dry mismatch (final state)              <= 0.5 % of cells
+  cells that arrived in one run but not the other <= 0.1 % of cells that arrived
+  arrival-time error (cells arrived in both)  mean <= 1 step, max <= 10 steps
+
+on C1 (single grid, 1800 steps), the C2 nest (1200 steps) and the three smallest grids
+of the C3 batch (2000 steps).
+"""
+import numpy as np
+import pytest
+
+from paper_2408_07609_gb300 import scenarios as S
+
+
+def _compare(rti, oracle_mod, sc, steps):
+    h = rti.Handle.from_scenario(sc, precision=rti.FP32)
+    h.step(steps)
+    h.sync()
+    o = oracle_mod.from_scenario(sc)
+    o.step(steps)
+    m = dict(eta=0.0, maxh=0.0, wet_mis=0, cells=0, arr_mis=0, arrived=0, arr_err=[])
+    for k, b in enumerate(sc.blocks):
+        hb = np.asarray(sc.bathy[k])
+        e32, e64 = h.get_state(k)[0], o.get_state(k)[0]
+        m["eta"] = max(m["eta"], float(np.abs(e32 - e64).max()))
+        g, r = h.max_height(k), o.max_height(k)
+        both = ~np.isnan(g) & ~np.isnan(r)
+        if both.any():
+            m["maxh"] = max(m["maxh"], float(np.abs(g[both] - r[both]).max()))
+        m["wet_mis"] += int(((hb + e32 > sc.dry_eps) != (hb + e64 > sc.dry_eps)).sum())
+        m["cells"] += hb.size
+        ga, ra = h.arrival_time(k), o.arrival_time(k)
+        ab = (ga >= 0) & (ra >= 0)
+        m["arr_err"].append(np.abs(ga[ab] - ra[ab]))
+        m["arr_mis"] += int(((ga >= 0) != (ra >= 0)).sum())
+        m["arrived"] += int((ra >= 0).sum())
+    h.close()
+    o.close()
+    m["arr_err"] = np.concatenate(m["arr_err"])
+    return m
+
+
+def _check(m, dt):
+    assert m["eta"] <= 0.05, m["eta"]
+    assert m["maxh"] <= 0.05, m["maxh"]
+    assert m["wet_mis"] <= 0.005 * m["cells"], m["wet_mis"]
+    assert m["arr_mis"] <= 0.001 * max(m["arrived"], 1), m["arr_mis"]
+    if m["arr_err"].size:
+        assert m["arr_err"].mean() <= dt and m["arr_err"].max() <= 10 * dt
+
+
+@pytest.mark.gpu
+def test_fp32_c1_single_grid(rti, oracle_mod):
+    sc = S.config1()
+    m = _compare(rti, oracle_mod, sc, sc.steps)
+    assert m["arrived"] > 1000
+    _check(m, sc.dt)
+
+
+@pytest.mark.gpu
+def test_fp32_c2_nest(rti, oracle_mod):
+    sc = S.config2(steps=1200)
+    m = _compare(rti, oracle_mod, sc, sc.steps)
+    _check(m, sc.dt)
+
+
+@pytest.mark.gpu
+def test_fp32_c3_smallest_grids(rti, oracle_mod):
+    grids = sorted(S.config3(), key=lambda s: s.cells)[:3]
+    for sc in grids:
+        m = _compare(rti, oracle_mod, sc, sc.steps)
+        _check(m, sc.dt)
