@@ -35,6 +35,11 @@ SIX_HOURS_STEPS = 108_000  # 6 h at dt = 0.2 s (Sec. V-A)
 # M^{n+1}, N^{n+1}; the rare eta_max / arrival writes are not counted.
 BYTES_PER_CELL_STEP = {"f32": 5 * 4 + 4 + 3 * 4,   # 36
                        "f64": 5 * 8 + 4 + 3 * 8}   # 68
+# DRAM bytes per cell-step that ncu measured for k_step<float> (dram__bytes_read.sum +
+# dram__bytes_write.sum of one single-step launch on the 7.95 M-cell 4-level hierarchy,
+# divided by its cells); scaled to a launch of the bench by cells x steps. Set to None
+# whenever the kernel changes until it is captured again.
+NCU_F32_DRAM_BYTES_PER_CELL_STEP = 305.36e6 / 7.95e6  # 38.4
 
 
 def parse():
@@ -55,6 +60,7 @@ def parse():
                     help="time scale of the serving trace (arrivals and durations)")
     ap.add_argument("--serve-pool-gb", type=int, default=32)
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -260,6 +266,38 @@ def serving(rti, sc5, a, world):
                                   "time per cell-step applied to every request of that kind"}}
 
 
+def batch_c3(rti, steps=200, warmup=5):
+    """C3: the 64 single grids (sides 128-1024, ~15.9 M cells) stepped together by one
+    batch (one persistent, graph-captured launch per chunk), CUDA events around the
+    steps, in FP32 and FP64."""
+    import torch
+
+    from paper_2408_07609_gb300 import scenarios as S
+
+    grids = S.config3(count=64, steps=steps + warmup)
+    cells = sum(g.cells for g in grids)
+    out = {"workload": f"64 grids, {cells / 1e6:.2f} M cells, chunk {steps} steps"}
+    for name, prec, n in (("fp32", rti.FP32, steps), ("fp64", rti.FP64, max(10, steps // 10))):
+        hs = [rti.Handle.from_scenario(g, precision=prec) for g in grids]
+        stream = torch.cuda.Stream()
+        b = rti.Batch(prec, rti.SCHED_PERSISTENT, n)
+        for h in hs:
+            b.add(h, n + n)
+        b.step(stream)  # warm-up chunk (uploads the tile list, captures the graph)
+        b.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(stream)
+        e1.record(stream)
+        b.sync()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"value": cells * n / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": n}
+        b.close()
+        for h in hs:
+            h.close()
+    return out
+
+
 def accuracy(rti):
     """FP32 against the FP64 path (which matches the FP64 oracle to 1e-12) on the 3-level
     C2 nest over its full hour: max |eta| and max-height error (m), wet/dry mismatch (%
@@ -348,6 +386,7 @@ def run_ours(a):
                            "and arrival of every block read back"}
     srv = None if a.no_serving else serving(rti, sc, a, world)
     acc = None if (a.no_accuracy or rank != 0) else accuracy(rti)
+    c3 = None if a.no_batch else batch_c3(rti)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         dt = cpu_baseline(sc, a.cpu_steps)
@@ -378,8 +417,13 @@ def run_ours(a):
             "gpu_launches": 3 if a.schedule == 0 else a.steps + 2,
             "serving": srv,
             "fp32_accuracy": acc,
+            "batch_c3": c3,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (None if NCU_F32_DRAM_BYTES_PER_CELL_STEP is None else
+                                     NCU_F32_DRAM_BYTES_PER_CELL_STEP * cells * a.steps),
+                         "traffic_note": "bytes per launch of the timed K steps, scaled from "
+                                         "a single-step ncu capture of the 4-level case",
                          "peak_kind": f"{kind} hbm_gbs",
                          "bytes_per_cell_step": bpc, "kernel": "k_step<float>"},
             "cpu_baseline": cpu,
