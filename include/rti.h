@@ -152,8 +152,9 @@ const char* rti_error_string(int code);
  * rti_last_error(NULL) says why.
  *
  * State layout (element type double for RTI_FP64, float for RTI_FP32; manning is always
- * float and arrival_step int): every array has `pitch` elements per row with
- * pitch >= nx + 9, and ny + 5 rows; element (column c, row r) lives at
+ * float and arrival_step int): every array starts on a 16-byte boundary and has `pitch`
+ * elements per row with pitch >= nx + 9 and a multiple of 4, and ny + 5 rows; element
+ * (column c, row r) lives at
  * (r + 2) * pitch + (c + 4). Cells use columns 0..nx-1 and rows 0..ny-1, M uses columns
  * 0..nx, N rows 0..ny. eta/M/N come in two time levels: level (steps_done & 1) is the
  * current one on entry, level ((steps_done + nsteps) & 1) on return. max_eta starts at

@@ -1235,8 +1235,8 @@ extern "C" int rti_step_noalloc(const rti_block* grid, const rti_params* params,
   for (int q = 0; q < 2; ++q)
     if (!state->eta[q] || !state->M[q] || !state->N[q]) return RTI_ERR_INVALID_ARG;
   if (!state->h || !state->manning || !state->max_eta || !state->arrival_step ||
-      state->pitch < grid->nx + 9) {
-    t_create_err = "rti_step_noalloc: null state array or pitch below nx + 9";
+      state->pitch < grid->nx + 9 || state->pitch % 4) {
+    t_create_err = "rti_step_noalloc: null state array, or pitch below nx + 9 or not a multiple of 4";
     return RTI_ERR_INVALID_ARG;
   }
   if (nsteps == 0) return RTI_OK;
@@ -1253,6 +1253,10 @@ extern "C" int rti_step_noalloc(const rti_block* grid, const rti_params* params,
           (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
         cudaGetLastError();
         t_create_err = "rti_step_noalloc: a state array is not device memory";
+        return RTI_ERR_INVALID_ARG;
+      }
+      if (reinterpret_cast<uintptr_t>(a) % 16) {
+        t_create_err = "rti_step_noalloc: a state array is not 16-byte aligned";
         return RTI_ERR_INVALID_ARG;
       }
     }

@@ -335,27 +335,67 @@ struct Raw {
   float nm;
 };
 
+// The march's input rows are staged ahead in shared memory: a ring of kRingD slots per
+// warp, each holding elements [x0 - 4, x0 + 32) of the six input rows of one row r.
+// 16-byte cp.async.cg copies (through L2, no registers held) keep kRingD - 1 rows per
+// warp in flight. A copy that would start past the allocated row is a zero fill.
+constexpr int kRingD = 6;
+constexpr int kRingW = 36;
+
 template <class T>
-__device__ __forceinline__ Raw<T> load_raw(const T* eta, const T* h, const T* M, const T* N,
-                                           const T* emax, const float* man, size_t o,
-                                           int pitch, bool ok) {
-  Raw<T> R;
-  if (ok) {
-    R.e = __ldcg(eta + o);
-    R.h = __ldcg(h + o);
-    R.m = __ldcg(M + o);
-    R.nn = __ldcg(N + o + pitch);
-    R.em = __ldcg(emax + o);
-    R.nm = __ldcg(man + o);
-  } else {
-    R.e = R.h = R.m = R.nn = R.em = T(0);
-    R.nm = 0.0f;
-  }
-  return R;
+struct __align__(16) RingSlot {
+  T e[kRingW], h[kRingW], m[kRingW], nn[kRingW], em[kRingW];
+  float nm[kRingW];
+};
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ bool lane_bit(unsigned mask, int lane, int d) {
-  return d < 0 ? ((mask << 1) >> lane) & 1u : ((mask >> lane) >> 1) & 1u;
+// Lanes issue the 16-byte chunks of row r (element `rowbase` = (r + 2) pitch + x0 is the
+// strip's column x0 - 4; N is taken one row up).
+template <class T>
+__device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T* h, const T* M,
+                                          const T* N, const T* emax, const float* man,
+                                          size_t rowbase, int pitch, int x0, int lane) {
+  constexpr int E = 16 / (int)sizeof(T);  // elements per chunk
+  if (lane < kRingW / E) {
+    const int k = lane * E;
+    const bool ok = x0 + k + E <= pitch;  // the chunk lies inside the allocated row
+    const size_t g = ok ? rowbase + k : rowbase;
+    cp_async16(&S.e[k], eta + g, ok);
+    cp_async16(&S.h[k], h + g, ok);
+    cp_async16(&S.m[k], M + g, ok);
+    cp_async16(&S.nn[k], N + g + pitch, ok);
+    cp_async16(&S.em[k], emax + g, ok);
+  }
+  if (lane < kRingW / 4) {
+    const int k = lane * 4;
+    const bool ok = x0 + k + 4 <= pitch;
+    cp_async16(&S.nm[k], man + (ok ? rowbase + k : rowbase), ok);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ Raw<T> read_row(const RingSlot<T>& S, int lane) {
+  Raw<T> R;
+  R.e = S.e[lane + 2];
+  R.h = S.h[lane + 2];
+  R.m = S.m[lane + 2];
+  R.nn = S.nn[lane + 2];
+  R.em = S.em[lane + 2];
+  R.nm = S.nm[lane + 2];
+  return R;
 }
 
 // R2 + R4 at x-face (c, j): cells W = (c-1, j), E = (c, j); QX of faces c-1, c, c+1
@@ -406,6 +446,28 @@ __device__ __forceinline__ T ymom_r(T hS, T eS, T hN, T eN, T v, T mb, bool okm,
   return keep ? lim : T(0);
 }
 
+// Both cells wet and every face of both upwind stencils usable (the open-water case):
+// the wet/dry cases and usable flags of xmom_r / ymom_r drop out. Same expressions, so
+// the same values as the general form under those conditions.
+template <class T>
+__device__ __forceinline__ T upwind_open(T w, T phim, T phi0, T phip) {
+  return w > T(0) ? phi0 - phim : (w < T(0) ? phip - phi0 : T(0.5) * (phip - phim));
+}
+template <class T>
+__device__ __forceinline__ T mom_open(T hA, T eA, T hB, T eB, T m, T across, T pm, T p0, T pp,
+                                      T qm, T q0, T qp, float nA, float nB, T eps, T dtdx, T g,
+                                      T cfric, T dx, T q4dt) {
+  const T Df = T(0.5) * (hA + hB) + T(0.5) * (eA + eB);
+  const T grad = eB - eA;
+  const T a1 = upwind_open(m, pm, p0, pp);
+  const T a2 = upwind_open(across, qm, q0, qp);
+  const T adv = dtdx * (a1 + a2);
+  const T nf = (T)(nA > nB ? nA : nB);
+  const T m1 = Ar<T>::update(m, across, Df, grad, adv, nf, g, dtdx, cfric);
+  const T lim = limit_outflow(m1, hA + eA, hB + eB, dx, q4dt);
+  return Df > eps ? lim : T(0);
+}
+
 // R6: flux leaving through a root edge next to a cell (sign +1 east/north, -1 west/south)
 template <class T>
 __device__ __forceinline__ T radiate_r(T h, T e, T sign, T eps, T g) {
@@ -417,6 +479,7 @@ __device__ __forceinline__ T radiate_r(T h, T e, T sign, T eps, T g) {
 // scenario counters and the index of the block staged.
 template <class T>
 struct WarpSlot {
+  RingSlot<T> ring[kRingD];
   Blk<T> b;
   Blk<T> P;
   ScenDev sc;
@@ -556,11 +619,17 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   bool bad = false;
   size_t o = (size_t)(y0 - 2 + kYOff) * (size_t)pitch + (size_t)(c + kXOff);
 
-  // prologue: N^n of y-face (c, y0 - 2) and the raw rows y0 - 2, y0 - 1
+  // prologue: N^n of y-face (c, y0 - 2); rows y0 - 2 .. y0 + kRingD - 4 staged
   T nS = col_ok ? __ldcg(Np + o) : T(0);  // y0 - 2 is below row 0 or an interior row
   T nSL = __shfl_up_sync(full, nS, 1);
-  Raw<T> R0 = load_raw(etaP, hh, Mp, Np, emax, man, o, pitch, col_ok);
-  Raw<T> R1 = load_raw(etaP, hh, Mp, Np, emax, man, o + pitch, pitch, col_ok);
+  const int x0 = td.x0;
+  size_t rowbase = (size_t)(y0 - 2 + kYOff) * (size_t)pitch + (size_t)x0;
+  for (int k = 0; k < kRingD - 1; ++k) {
+    if (y0 - 2 + k <= ye)
+      stage_row(ws.ring[k], etaP, hh, Mp, Np, emax, man, rowbase + (size_t)k * pitch, pitch, x0,
+                lane);
+    cp_async_commit();
+  }
   Row<T> A = {}, B = {}, C = {};
 
   // One row r from its inputs `cur`: X receives row r; Y, Z are rows r - 2, r - 1.
@@ -641,20 +710,31 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     // ---- row j = r - 1 (rows Y, Z, X = j-1, j, j+1): M^{n+1}, N^{n+1} (R2-R4), root edges (R6)
     if (r > y0) {
       const int j = r - 1;
-      // a warp whose cells on both sides of every owned face are dry updates nothing
-      const bool act = own_col && (Z.hL + Z.eL > eps || Z.H + Z.E > eps || Y.H + Y.E > eps);
+      // a warp whose cells on both sides of every owned face are dry updates nothing;
+      // one whose owned faces are all in open water takes the short form
+      const bool wA = Y.H + Y.E > eps, wB = Z.H + Z.E > eps, wW = Z.hL + Z.eL > eps;
+      const bool act = own_col && (wW || wB || wA);
       T xm = T(0), ym = T(0);
       if (__any_sync(full, act)) {
         const T qm = __shfl_up_sync(full, Z.QX, 1), qp = __shfl_down_sync(full, Z.QX, 1);
         const T tw = __shfl_up_sync(full, Z.TY, 1), te = __shfl_down_sync(full, Z.TY, 1);
         const float nmL = __shfl_up_sync(full, Z.nm, 1);
         const unsigned bx = __ballot_sync(full, Z.vx), by = __ballot_sync(full, Z.vy);
-        xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, ((bx >> sl) & 1u) != 0, qm, Z.QX,
-                    ((bx >> sr) & 1u) != 0, qp, Y.vx, Y.RX, Z.RX, X.vx, X.RX, nmL, Z.nm, eps,
-                    dtdx, g, cfric, dx, q4dt);
-        ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.vy, Y.SY, Z.SY, X.vy, X.SY,
-                    ((by >> sl) & 1u) != 0, tw, Z.TY, ((by >> sr) & 1u) != 0, te, Y.nm, Z.nm,
-                    eps, dtdx, g, cfric, dx, q4dt);
+        const bool xm_ok = ((bx >> sl) & 1u) != 0, xp_ok = ((bx >> sr) & 1u) != 0;
+        const bool yw_ok = ((by >> sl) & 1u) != 0, ye_ok = ((by >> sr) & 1u) != 0;
+        const bool open = !own_col || (wW && wB && wA && xm_ok && xp_ok && Y.vx && X.vx &&
+                                       yw_ok && ye_ok && Y.vy && X.vy);
+        if (__all_sync(full, open)) {
+          xm = mom_open(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, qm, Z.QX, qp, Y.RX, Z.RX, X.RX, nmL,
+                        Z.nm, eps, dtdx, g, cfric, dx, q4dt);
+          ym = mom_open(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.SY, Z.SY, X.SY, tw, Z.TY, te, Y.nm,
+                        Z.nm, eps, dtdx, g, cfric, dx, q4dt);
+        } else {
+          xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, xm_ok, qm, Z.QX, xp_ok, qp, Y.vx, Y.RX,
+                      Z.RX, X.vx, X.RX, nmL, Z.nm, eps, dtdx, g, cfric, dx, q4dt);
+          ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.vy, Y.SY, Z.SY, X.vy, X.SY, yw_ok, tw,
+                      Z.TY, ye_ok, te, Y.nm, Z.nm, eps, dtdx, g, cfric, dx, q4dt);
+        }
       }
       if (own_col) {
         const size_t oj = o - (size_t)pitch;
@@ -671,16 +751,27 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     o += pitch;
   };
 
+  int slot = 0;  // ring slot of row r
   for (int r = y0 - 2; r <= ye; ++r) {
-    const Raw<T> cur = R0;
-    R0 = R1;
-    if (r + 2 <= ye) R1 = load_raw(etaP, hh, Mp, Np, emax, man, o + 2 * (size_t)pitch, pitch, col_ok);
+    __syncwarp();  // every lane has read the slot of row r - 1 before it is refilled
+    if (r + kRingD - 1 <= ye)
+      stage_row(ws.ring[slot == 0 ? kRingD - 1 : slot - 1], etaP, hh, Mp, Np, emax, man,
+                rowbase + (size_t)(kRingD - 1) * pitch, pitch, x0, lane);
+    cp_async_commit();
+    cp_async_wait<kRingD - 1>();  // row r has landed
+    __syncwarp();                 // ... for every lane's chunks
+    const Raw<T> cur = read_row(ws.ring[slot], lane);
+    slot = slot + 1 == kRingD ? 0 : slot + 1;
+    rowbase += pitch;
     Row<T> X;
     row(cur, X, B, C, r);
     A = B;  // rows r-2, r-1, r
     B = C;
     C = X;
   }
+
+  cp_async_wait<0>();  // (only empty groups can be outstanding here)
+  __syncwarp();
 
   // ---- the strip's budget partials (binary64, fixed reduction order)
   if (bad) atomicOr(b.status, kStNonFinite);
@@ -744,8 +835,20 @@ __device__ __forceinline__ bool grid_barrier(Bar* bar, unsigned& gen, int* statu
 // (step s - 1 has ended: a barrier or the previous launch lies between). With more
 // than one step the launch must be cooperative: consecutive steps are separated by the
 // device-wide barrier.
+// Resident CTAs per SM the register allocation targets: binary32 fits 96 registers
+// (5 CTAs of 4 warps) without spilling; binary64 keeps the compiler's choice.
 template <class T>
-__global__ void __launch_bounds__(kWarps * 32) k_step(KParams<T> kp, int s_first, int s_count) {
+struct StepOcc {
+  static constexpr int kMinBlocks = 1;
+};
+template <>
+struct StepOcc<float> {
+  static constexpr int kMinBlocks = 5;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
+    k_step(KParams<T> kp, int s_first, int s_count) {
   __shared__ WarpSlot<T> slots[kWarps];
   __shared__ int go;
   WarpSlot<T>& ws = slots[threadIdx.y];
