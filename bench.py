@@ -99,6 +99,12 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def whole_job_rate(cells, steps, ms, world):
+    """GCUPS of the whole job: every rank steps its own copy of the workload, and the
+    job takes as long as its slowest rank."""
+    return world * cells * steps / (ms / 1e3) / 1e9
+
+
 class Clocks:
     """nvidia-smi samples (SM clock, throttle reasons) while the timed region runs."""
 
@@ -371,8 +377,8 @@ def run_ours(a):
                        a.tile)
     ms64 = max_over_ranks(ms64, world)
     per32, per64 = ms32 / a.steps, ms64 / a.fp64_steps
-    gcups32 = world * cells * a.steps / (ms32 / 1e3) / 1e9
-    gcups64 = world * cells * a.fp64_steps / (ms64 / 1e3) / 1e9
+    gcups32 = whole_job_rate(cells, a.steps, ms32, world)
+    gcups64 = whole_job_rate(cells, a.fp64_steps, ms64, world)
     peak, kind = peaks()
     bpc = BYTES_PER_CELL_STEP["f32"]
     achieved = bpc * cells * a.steps / (ms32 / 1e3) / 1e9  # GB/s of one launch of K steps
