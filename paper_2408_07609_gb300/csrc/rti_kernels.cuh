@@ -719,21 +719,24 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
         const T qm = __shfl_up_sync(full, Z.QX, 1), qp = __shfl_down_sync(full, Z.QX, 1);
         const T tw = __shfl_up_sync(full, Z.TY, 1), te = __shfl_down_sync(full, Z.TY, 1);
         const float nmL = __shfl_up_sync(full, Z.nm, 1);
-        const unsigned bx = __ballot_sync(full, Z.vx), by = __ballot_sync(full, Z.vy);
-        const bool xm_ok = ((bx >> sl) & 1u) != 0, xp_ok = ((bx >> sr) & 1u) != 0;
-        const bool yw_ok = ((by >> sl) & 1u) != 0, ye_ok = ((by >> sr) & 1u) != 0;
-        const bool open = !own_col || (wW && wB && wA && xm_ok && xp_ok && Y.vx && X.vx &&
-                                       yw_ok && ye_ok && Y.vy && X.vy);
+        // open water for the whole warp: the faces of lanes 1..30 (the owned lanes and
+        // their neighbours) are usable and every owned face has wet cells on both sides
+        const bool open = lane == 0 || lane == 31 ||
+                          (Z.vx && Z.vy && (!own_col || (wW && wB && wA && Y.vx && X.vx &&
+                                                         Y.vy && X.vy)));
         if (__all_sync(full, open)) {
           xm = mom_open(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, qm, Z.QX, qp, Y.RX, Z.RX, X.RX, nmL,
                         Z.nm, eps, dtdx, g, cfric, dx, q4dt);
           ym = mom_open(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.SY, Z.SY, X.SY, tw, Z.TY, te, Y.nm,
                         Z.nm, eps, dtdx, g, cfric, dx, q4dt);
         } else {
-          xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, xm_ok, qm, Z.QX, xp_ok, qp, Y.vx, Y.RX,
-                      Z.RX, X.vx, X.RX, nmL, Z.nm, eps, dtdx, g, cfric, dx, q4dt);
-          ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.vy, Y.SY, Z.SY, X.vy, X.SY, yw_ok, tw,
-                      Z.TY, ye_ok, te, Y.nm, Z.nm, eps, dtdx, g, cfric, dx, q4dt);
+          const unsigned bx = __ballot_sync(full, Z.vx), by = __ballot_sync(full, Z.vy);
+          xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, ((bx >> sl) & 1u) != 0, qm, Z.QX,
+                      ((bx >> sr) & 1u) != 0, qp, Y.vx, Y.RX, Z.RX, X.vx, X.RX, nmL, Z.nm, eps,
+                      dtdx, g, cfric, dx, q4dt);
+          ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.vy, Y.SY, Z.SY, X.vy, X.SY,
+                      ((by >> sl) & 1u) != 0, tw, Z.TY, ((by >> sr) & 1u) != 0, te, Y.nm, Z.nm,
+                      eps, dtdx, g, cfric, dx, q4dt);
         }
       }
       if (own_col) {
