@@ -616,7 +616,6 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   // adds; the strip's sums are formed and scaled in binary64 at the end)
   T vol_t = T(0), clip_t = T(0), out_t = T(0), ring_t = T(0);
   const bool edge_strip = td.x0 == 0 || td.x0 + kStripW >= nx || y0 == 0 || ye == ny;
-  bool bad = false;
   size_t o = (size_t)(y0 - 2 + kYOff) * (size_t)pitch + (size_t)(c + kXOff);
 
   // prologue: N^n of y-face (c, y0 - 2); rows y0 - 2 .. y0 + kRingD - 4 staged
@@ -666,8 +665,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
         if (em < thr && e >= thr) b.arr[o] = sn;
         emax[o] = e;
       }
-      vol_t += e;
-      bad |= !dfinite(e);
+      vol_t += e;  // a non-finite level makes the strip's sum non-finite
       if (edge_strip) {  // flux through the block's edges (outflow positive)
         T of = T(0);
         if (c == 0) of -= m;
@@ -686,11 +684,12 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
       const bool in = col_x && rin_x;
       Nw.vx = in && dep > eps;
       Nw.nb = T(0.25) * ((nSL + nS) + (nnL + nn));
+      // Binary32 divides everywhere: a face without a usable depth gets a value that
+      // every reader masks (usable flags) or discards (no wet pair on its own face).
       T qx = T(0), rx = T(0);
-      const bool use = in && dep != T(0);
-      if (Ar<T>::kSelect || use) Ar<T>::quot2(m * m, m * Nw.nb, dep, qx, rx);
-      Nw.QX = use ? qx : T(0);
-      Nw.RX = use ? rx : T(0);
+      if (Ar<T>::kSelect || (in && dep != T(0))) Ar<T>::quot2(m * m, m * Nw.nb, dep, qx, rx);
+      Nw.QX = qx;
+      Nw.RX = rx;
     }
     {  // y-face (c, r)
       const T dep = T(0.5) * (Z.H + Nw.H) + T(0.5) * (Z.E + Nw.E);
@@ -698,10 +697,9 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
       Nw.vy = in && dep > eps;
       Nw.mb = T(0.25) * ((Z.MX + m) + (Z.mE + Nw.mE));
       T sy = T(0), ty = T(0);
-      const bool use = in && dep != T(0);
-      if (Ar<T>::kSelect || use) Ar<T>::quot2(nS * nS, nS * Nw.mb, dep, sy, ty);
-      Nw.SY = use ? sy : T(0);
-      Nw.TY = use ? ty : T(0);
+      if (Ar<T>::kSelect || (in && dep != T(0))) Ar<T>::quot2(nS * nS, nS * Nw.mb, dep, sy, ty);
+      Nw.SY = sy;
+      Nw.TY = ty;
     }
     X = Nw;
     nS = nn;
@@ -777,8 +775,8 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   __syncwarp();
 
   // ---- the strip's budget partials (binary64, fixed reduction order)
-  if (bad) atomicOr(b.status, kStNonFinite);
   const double vs = warp_sum((double)vol_t);
+  if (lane == 0 && !dfinite(vs)) atomicOr(b.status, kStNonFinite);
   const double cs = warp_sum((double)clip_t) * b.dx2, os = warp_sum((double)out_t) * b.vol,
                rs = warp_sum((double)ring_t) * b.dx2;
   if (lane == 0) {
