@@ -229,6 +229,29 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Constants of the momentum update of one block, formed once per strip: binary64 keeps
+// the oracle's factors, binary32 folds the loop-invariant products and quotient.
+template <class T>
+struct MomK;
+template <>
+struct MomK<double> {
+  double eps, dtdx, g, cfric, dx, q4dt;
+};
+template <>
+struct MomK<float> {
+  float eps, dtdx, gdtdx /* g dt/dx */, cfric, dxq /* dx / (4 dt) */;
+};
+template <class T>
+__device__ __forceinline__ MomK<T> mom_consts(const Blk<T>& b);
+template <>
+__device__ __forceinline__ MomK<double> mom_consts(const Blk<double>& b) {
+  return MomK<double>{b.eps, b.dtdx, b.g, b.cfric, b.dx, b.q4dt};
+}
+template <>
+__device__ __forceinline__ MomK<float> mom_consts(const Blk<float>& b) {
+  return MomK<float>{b.eps, b.dtdx, b.g * b.dtdx, b.cfric, b.dx / b.q4dt};
+}
+
 template <class T>
 struct Ar;
 template <>
@@ -241,10 +264,18 @@ struct Ar<double> {
   }
   static __device__ __forceinline__ double update(double m, double across, double Df,
                                                   double grad, double adv, double nf,
-                                                  double g, double dtdx, double cfric) {
-    double P = g * Df * dtdx * grad;
-    double F = cfric * nf * nf * sqrt(m * m + across * across) / (Df * Df * cbrt(Df));
+                                                  const MomK<double>& K) {
+    double P = K.g * Df * K.dtdx * grad;
+    double F = K.cfric * nf * nf * sqrt(m * m + across * across) / (Df * Df * cbrt(Df));
     return ((1.0 - F) * m - adv - P) / (1.0 + F);
+  }
+  // Outflow limit: |flux| <= D dx / (4 dt) with D the depth of the cell it drains.
+  static __device__ __forceinline__ double limit(double m, double Dlo, double Dhi,
+                                                 const MomK<double>& K) {
+    const double cap = (m > 0.0 ? Dlo : Dhi) * K.dx / K.q4dt;
+    if (m > cap) return cap;
+    if (m < -cap) return -cap;
+    return m;
   }
 };
 template <>
@@ -257,39 +288,21 @@ struct Ar<float> {
     q2 = a2 * r;
   }
   static __device__ __forceinline__ float update(float m, float across, float Df, float grad,
-                                                 float adv, float nf, float g, float dtdx,
-                                                 float cfric) {
-    const float P = (g * dtdx) * Df * grad;
+                                                 float adv, float nf, const MomK<float>& K) {
+    const float P = K.gdtdx * Df * grad;
     const float s2 = m * m + across * across;
     const float F =
-        (cfric * nf * nf) * ex2_approx(0.5f * lg2_approx(s2) - 2.33333333f * lg2_approx(Df));
+        (K.cfric * nf * nf) * ex2_approx(0.5f * lg2_approx(s2) - 2.33333333f * lg2_approx(Df));
     return __fdividef((1.0f - F) * m - adv - P, 1.0f + F);
   }
+  static __device__ __forceinline__ float limit(float m, float Dlo, float Dhi,
+                                                const MomK<float>& K) {
+    const float cap = (m > 0.0f ? Dlo : Dhi) * K.dxq;
+    if (m > cap) return cap;  // (a NaN passes through, for the non-finite check)
+    if (m < -cap) return -cap;
+    return m;
+  }
 };
-
-template <class T>
-__device__ __forceinline__ T flux_update(const Blk<T>& b, T m, T across, T Df, T grad, T adv,
-                                         T nf) {
-  return Ar<T>::update(m, across, Df, grad, adv, nf, b.g, b.dtdx, b.cfric);
-}
-
-// Outflow limit: |flux| <= D dx / (4 dt) with D the depth of the cell it drains.
-// Binary64 keeps the oracle's expression; binary32 multiplies by dx / (4 dt), which the
-// compiler hoists out of the march.
-__device__ __forceinline__ double limit_outflow(double m, double Dlo, double Dhi, double dx,
-                                                double q4dt) {
-  const double cap = (m > 0.0 ? Dlo : Dhi) * dx / q4dt;
-  if (m > cap) return cap;
-  if (m < -cap) return -cap;
-  return m;
-}
-__device__ __forceinline__ float limit_outflow(float m, float Dlo, float Dhi, float dx,
-                                               float q4dt) {
-  const float cap = (m > 0.0f ? Dlo : Dhi) * (dx / q4dt);
-  if (m > cap) return cap;
-  if (m < -cap) return -cap;
-  return m;
-}
 
 // ------------------------------------------------------------------ block reduction
 __device__ __forceinline__ double warp_sum(double v) {
@@ -405,8 +418,8 @@ __device__ __forceinline__ Raw<T> read_row(const RingSlot<T>& S, int lane) {
 template <class T>
 __device__ __forceinline__ T xmom_r(T hL, T eL, T hR, T eR, T m, T nb, bool okm, T qm, T q0,
                                     bool okp, T qp, bool oks, T rs, T r0, bool okn, T rn,
-                                    float nL, float nR, T eps, T dtdx, T g, T cfric, T dx,
-                                    T q4dt) {
+                                    float nL, float nR, const MomK<T>& K) {
+  const T eps = K.eps, dtdx = K.dtdx;
   const bool wL = hL + eL > eps, wR = hR + eR > eps;
   const bool both = wL && wR;
   const bool oneL = wL && !wR && eL > -hR;  // water flows onto the dry east cell
@@ -417,9 +430,9 @@ __device__ __forceinline__ T xmom_r(T hL, T eL, T hR, T eR, T m, T nb, bool okm,
   const T ay = upwind(nb, oks ? rs : T(0), r0, okn ? rn : T(0), oks, okn);
   const T adv = both ? dtdx * (ax + ay) : T(0);
   const T nf = (T)(nL > nR ? nL : nR);
-  const T m1 = Ar<T>::update(m, nb, Df, grad, adv, nf, g, dtdx, cfric);
+  const T m1 = Ar<T>::update(m, nb, Df, grad, adv, nf, K);
   const bool keep = (both || oneL || oneR) && Df > eps && (both || (wL ? !(m1 < T(0)) : !(m1 > T(0))));
-  const T lim = limit_outflow(m1, hL + eL, hR + eR, dx, q4dt);
+  const T lim = Ar<T>::limit(m1, hL + eL, hR + eR, K);
   return keep ? lim : T(0);
 }
 
@@ -428,8 +441,8 @@ __device__ __forceinline__ T xmom_r(T hL, T eL, T hR, T eR, T m, T nb, bool okm,
 template <class T>
 __device__ __forceinline__ T ymom_r(T hS, T eS, T hN, T eN, T v, T mb, bool okm, T sm, T s0,
                                     bool okp, T sp, bool okw, T tw, T t0, bool oke, T te,
-                                    float nS, float nN, T eps, T dtdx, T g, T cfric, T dx,
-                                    T q4dt) {
+                                    float nS, float nN, const MomK<T>& K) {
+  const T eps = K.eps, dtdx = K.dtdx;
   const bool wS = hS + eS > eps, wN = hN + eN > eps;
   const bool both = wS && wN;
   const bool oneS = wS && !wN && eS > -hN;
@@ -440,9 +453,9 @@ __device__ __forceinline__ T ymom_r(T hS, T eS, T hN, T eN, T v, T mb, bool okm,
   const T ax = upwind(mb, okw ? tw : T(0), t0, oke ? te : T(0), okw, oke);
   const T adv = both ? dtdx * (ay + ax) : T(0);
   const T nf = (T)(nS > nN ? nS : nN);
-  const T v1 = Ar<T>::update(v, mb, Df, grad, adv, nf, g, dtdx, cfric);
+  const T v1 = Ar<T>::update(v, mb, Df, grad, adv, nf, K);
   const bool keep = (both || oneS || oneN) && Df > eps && (both || (wS ? !(v1 < T(0)) : !(v1 > T(0))));
-  const T lim = limit_outflow(v1, hS + eS, hN + eN, dx, q4dt);
+  const T lim = Ar<T>::limit(v1, hS + eS, hN + eN, K);
   return keep ? lim : T(0);
 }
 
@@ -455,17 +468,16 @@ __device__ __forceinline__ T upwind_open(T w, T phim, T phi0, T phip) {
 }
 template <class T>
 __device__ __forceinline__ T mom_open(T hA, T eA, T hB, T eB, T m, T across, T pm, T p0, T pp,
-                                      T qm, T q0, T qp, float nA, float nB, T eps, T dtdx, T g,
-                                      T cfric, T dx, T q4dt) {
+                                      T qm, T q0, T qp, float nA, float nB, const MomK<T>& K) {
   const T Df = T(0.5) * (hA + hB) + T(0.5) * (eA + eB);
   const T grad = eB - eA;
   const T a1 = upwind_open(m, pm, p0, pp);
   const T a2 = upwind_open(across, qm, q0, qp);
-  const T adv = dtdx * (a1 + a2);
+  const T adv = K.dtdx * (a1 + a2);
   const T nf = (T)(nA > nB ? nA : nB);
-  const T m1 = Ar<T>::update(m, across, Df, grad, adv, nf, g, dtdx, cfric);
-  const T lim = limit_outflow(m1, hA + eA, hB + eB, dx, q4dt);
-  return Df > eps ? lim : T(0);
+  const T m1 = Ar<T>::update(m, across, Df, grad, adv, nf, K);
+  const T lim = Ar<T>::limit(m1, hA + eA, hB + eB, K);
+  return Df > K.eps ? lim : T(0);
 }
 
 // R6: flux leaving through a root edge next to a cell (sign +1 east/north, -1 west/south)
@@ -591,7 +603,8 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   // the descriptor fields of the march, as locals
   const int nx = b.nx, ny = b.ny, pitch = b.pitch;
   const bool root = !b.is_child;
-  const T dtdx = b.dtdx, eps = b.eps, g = b.g, cfric = b.cfric, dx = b.dx, q4dt = b.q4dt;
+  const T dtdx = b.dtdx, eps = b.eps, g = b.g;
+  const MomK<T> K = mom_consts(b);
   const T thr = b.thr;
   const T* etaP = b.eta[p];
   const T* Mp = b.M[p];
@@ -724,17 +737,16 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
                                                          Y.vy && X.vy)));
         if (__all_sync(full, open)) {
           xm = mom_open(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, qm, Z.QX, qp, Y.RX, Z.RX, X.RX, nmL,
-                        Z.nm, eps, dtdx, g, cfric, dx, q4dt);
+                        Z.nm, K);
           ym = mom_open(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.SY, Z.SY, X.SY, tw, Z.TY, te, Y.nm,
-                        Z.nm, eps, dtdx, g, cfric, dx, q4dt);
+                        Z.nm, K);
         } else {
           const unsigned bx = __ballot_sync(full, Z.vx), by = __ballot_sync(full, Z.vy);
           xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, ((bx >> sl) & 1u) != 0, qm, Z.QX,
-                      ((bx >> sr) & 1u) != 0, qp, Y.vx, Y.RX, Z.RX, X.vx, X.RX, nmL, Z.nm, eps,
-                      dtdx, g, cfric, dx, q4dt);
+                      ((bx >> sr) & 1u) != 0, qp, Y.vx, Y.RX, Z.RX, X.vx, X.RX, nmL, Z.nm, K);
           ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.vy, Y.SY, Z.SY, X.vy, X.SY,
                       ((by >> sl) & 1u) != 0, tw, Z.TY, ((by >> sr) & 1u) != 0, te, Y.nm, Z.nm,
-                      eps, dtdx, g, cfric, dx, q4dt);
+                      K);
         }
       }
       if (own_col) {
