@@ -659,10 +659,9 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     const T nnL = __shfl_up_sync(full, nn, 1);
     T e = cur.e - (dtdx * (Nw.mE - m) + dtdx * (nn - nS));
     const bool own = own_col && r >= y0 && r < ye;
-    if (Nw.H + e < T(0)) {
-      clip_t += own ? -Nw.H - e : T(0);
-      e = -Nw.H;
-    }
+    const bool clipped = Nw.H + e < T(0);
+    clip_t += (clipped && own) ? -Nw.H - e : T(0);
+    e = clipped ? -Nw.H : e;
     if (ring_strip) {  // fine-to-coarse override (R8), formed by the prepass
       const T rv = col_ok ? __ldcg(b.ring + o) : ring_none(T(0));
       if (!ring_unset(rv) && col_y && rin_x) {
@@ -671,22 +670,22 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
       }
     }
     Nw.E = e;
-    if (own) {
-      etaQ[o] = e;
+    {  // output update (predicated stores, no branches)
       const T em = cur.em;
-      if (Nw.H + e > eps && e > em) {
-        if (em < thr && e >= thr) b.arr[o] = sn;
-        emax[o] = e;
-      }
-      vol_t += e;  // a non-finite level makes the strip's sum non-finite
-      if (edge_strip) {  // flux through the block's edges (outflow positive)
-        T of = T(0);
-        if (c == 0) of -= m;
-        if (c == nx - 1) of += Nw.mE;
-        if (r == 0) of -= nS;
-        if (r == ny - 1) of += nn;
-        out_t += of;
-      }
+      const bool up = own && Nw.H + e > eps && e > em;
+      const bool arrives = up && em < thr && e >= thr;
+      if (own) etaQ[o] = e;
+      if (up) emax[o] = e;
+      if (arrives) b.arr[o] = sn;
+      vol_t += own ? e : T(0);  // a non-finite level makes the strip's sum non-finite
+    }
+    if (edge_strip) {  // flux through the block's edges (outflow positive)
+      T of = T(0);
+      of -= (own && c == 0) ? m : T(0);
+      of += (own && c == nx - 1) ? Nw.mE : T(0);
+      of -= (own && r == 0) ? nS : T(0);
+      of += (own && r == ny - 1) ? nn : T(0);
+      out_t += of;
     }
 
     // ---- advective face terms of row r
@@ -749,7 +748,12 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
                       K);
         }
       }
-      if (own_col) {
+      if (!edge_strip) {  // interior strip: every owned face is an interior face
+        if (own_col) {
+          Mq[o - (size_t)pitch] = xm;
+          Nq[o - (size_t)pitch] = ym;
+        }
+      } else if (own_col) {
         const size_t oj = o - (size_t)pitch;
         if (c >= 1) Mq[oj] = xm;
         else if (root) Mq[oj] = b.bc[0] == kBcRadiation ? radiate_r(Z.H, Z.E, T(-1), eps, g) : T(0);
