@@ -55,7 +55,8 @@ extern "C" {
 typedef struct {
   int level;  /* 1 for the root level, parent level + 1 otherwise */
   int parent; /* index of the parent block in the same array, -1 for a root */
-  int nx, ny; /* cells; multiples of 3 for a child */
+  int nx, ny; /* cells, 3 .. 2^20 each and (nx + 9 rounded up to 32) x (ny + 5) < 2^31;
+                 multiples of 3 for a child */
   int i0, j0; /* child origin in parent cells; the child covers nx/3 x ny/3 parent cells */
   double dx;  /* cell size in metres; a child has exactly its parent's dx / 3 */
   int bc[4];  /* west, east, south, north edge of a root block: RTI_BC_*; ignored for children */
@@ -153,7 +154,8 @@ const char* rti_error_string(int code);
  *
  * State layout (element type double for RTI_FP64, float for RTI_FP32; manning is always
  * float and arrival_step int): every array starts on a 16-byte boundary and has `pitch`
- * elements per row with pitch >= nx + 9 and a multiple of 4, and ny + 5 rows; element
+ * elements per row with pitch >= nx + 9 and a multiple of 4, and ny + 5 rows, with
+ * pitch x (ny + 5) < 2^31; element
  * (column c, row r) lives at
  * (r + 2) * pitch + (c + 4). Cells use columns 0..nx-1 and rows 0..ny-1, M uses columns
  * 0..nx, N rows 0..ny. eta/M/N come in two time levels: level (steps_done & 1) is the

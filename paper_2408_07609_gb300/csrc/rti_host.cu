@@ -103,6 +103,11 @@ int validate(const rti_block* bl, int nb, const rti_params* p, std::string* why)
       *why = "block " + std::to_string(k) + ": bad size or dx";
       return RTI_ERR_INVALID_ARG;
     }
+    // the kernels index a plane with 32-bit element offsets
+    if ((long long)pitch_for(d->nx) * rows_for(d->ny) >= (1LL << 31)) {
+      *why = "block " + std::to_string(k) + ": more than 2^31 elements per plane";
+      return RTI_ERR_INVALID_ARG;
+    }
     if (d->parent < 0) {
       if (d->level != 1) {
         *why = "block " + std::to_string(k) + ": a root must have level 1";
@@ -1235,8 +1240,10 @@ extern "C" int rti_step_noalloc(const rti_block* grid, const rti_params* params,
   for (int q = 0; q < 2; ++q)
     if (!state->eta[q] || !state->M[q] || !state->N[q]) return RTI_ERR_INVALID_ARG;
   if (!state->h || !state->manning || !state->max_eta || !state->arrival_step ||
-      state->pitch < grid->nx + 9 || state->pitch % 4) {
-    t_create_err = "rti_step_noalloc: null state array, or pitch below nx + 9 or not a multiple of 4";
+      state->pitch < grid->nx + 9 || state->pitch % 4 ||
+      (long long)state->pitch * rows_for(grid->ny) >= (1LL << 31)) {
+    t_create_err = "rti_step_noalloc: null state array, or pitch below nx + 9, not a multiple of 4 "
+                   "or too large (pitch x (ny + 5) must stay below 2^31)";
     return RTI_ERR_INVALID_ARG;
   }
   if (nsteps == 0) return RTI_OK;

@@ -380,12 +380,12 @@ __device__ __forceinline__ void cp_async_wait() {
 template <class T>
 __device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T* h, const T* M,
                                           const T* N, const T* emax, const float* man,
-                                          size_t rowbase, int pitch, int x0, int lane) {
+                                          int rowbase, int pitch, int x0, int lane) {
   constexpr int E = 16 / (int)sizeof(T);  // elements per chunk
   if (lane < kRingW / E) {
     const int k = lane * E;
     const bool ok = x0 + k + E <= pitch;  // the chunk lies inside the allocated row
-    const size_t g = ok ? rowbase + k : rowbase;
+    const int g = ok ? rowbase + k : rowbase;
     cp_async16(&S.e[k], eta + g, ok);
     cp_async16(&S.h[k], h + g, ok);
     cp_async16(&S.m[k], M + g, ok);
@@ -629,16 +629,17 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   // adds; the strip's sums are formed and scaled in binary64 at the end)
   T vol_t = T(0), clip_t = T(0), out_t = T(0), ring_t = T(0);
   const bool edge_strip = td.x0 == 0 || td.x0 + kStripW >= nx || y0 == 0 || ye == ny;
-  size_t o = (size_t)(y0 - 2 + kYOff) * (size_t)pitch + (size_t)(c + kXOff);
+  // element offsets within a plane fit in 32 bits (rti_create checks pitch x rows < 2^31)
+  int o = (y0 - 2 + kYOff) * pitch + (c + kXOff);
 
   // prologue: N^n of y-face (c, y0 - 2); rows y0 - 2 .. y0 + kRingD - 4 staged
   T nS = col_ok ? __ldcg(Np + o) : T(0);  // y0 - 2 is below row 0 or an interior row
   T nSL = __shfl_up_sync(full, nS, 1);
   const int x0 = td.x0;
-  size_t rowbase = (size_t)(y0 - 2 + kYOff) * (size_t)pitch + (size_t)x0;
+  int rowbase = (y0 - 2 + kYOff) * pitch + x0;
   for (int k = 0; k < kRingD - 1; ++k) {
     if (y0 - 2 + k <= ye)
-      stage_row(ws.ring[k], etaP, hh, Mp, Np, emax, man, rowbase + (size_t)k * pitch, pitch, x0,
+      stage_row(ws.ring[k], etaP, hh, Mp, Np, emax, man, rowbase + k * pitch, pitch, x0,
                 lane);
     cp_async_commit();
   }
@@ -750,11 +751,11 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
       }
       if (!edge_strip) {  // interior strip: every owned face is an interior face
         if (own_col) {
-          Mq[o - (size_t)pitch] = xm;
-          Nq[o - (size_t)pitch] = ym;
+          Mq[o - pitch] = xm;
+          Nq[o - pitch] = ym;
         }
       } else if (own_col) {
-        const size_t oj = o - (size_t)pitch;
+        const int oj = o - pitch;
         if (c >= 1) Mq[oj] = xm;
         else if (root) Mq[oj] = b.bc[0] == kBcRadiation ? radiate_r(Z.H, Z.E, T(-1), eps, g) : T(0);
         if (c == nx - 1 && root)
@@ -773,7 +774,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     __syncwarp();  // every lane has read the slot of row r - 1 before it is refilled
     if (r + kRingD - 1 <= ye)
       stage_row(ws.ring[slot == 0 ? kRingD - 1 : slot - 1], etaP, hh, Mp, Np, emax, man,
-                rowbase + (size_t)(kRingD - 1) * pitch, pitch, x0, lane);
+                rowbase + (kRingD - 1) * pitch, pitch, x0, lane);
     cp_async_commit();
     cp_async_wait<kRingD - 1>();  // row r has landed
     __syncwarp();                 // ... for every lane's chunks

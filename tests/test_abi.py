@@ -66,3 +66,14 @@ def test_error_strings(rti):
     L = rti.lib()
     for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert L.rti_error_string(code)
+
+
+def test_planes_beyond_32_bit_offsets_are_rejected(rti):
+    """The kernels index a plane with 32-bit element offsets: a block whose padded plane
+    has 2^31 elements or more is refused on the host."""
+    big = blk(nx=1 << 20, ny=4096)
+    with pytest.raises(rti.RtiError) as e:
+        rti.footprint([big], rti.make_params(dt=0.5))
+    assert e.value.code == -1
+    ok = blk(nx=(1 << 20) - 9, ny=2040)  # pitch 2^20, 2045 rows: 2^31 - 3 x 2^20 elements
+    assert rti.footprint([ok], rti.make_params(dt=0.5, precision=rti.FP32)) > 0
