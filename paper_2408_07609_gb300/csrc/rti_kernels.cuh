@@ -361,11 +361,16 @@ struct __align__(16) RingSlot {
   float nm[kRingW];
 };
 
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+// One 16-byte copy, issued only where `issue` holds (a predicate on the instruction, not
+// a branch); `valid` false makes it a zero fill that reads nothing.
+__device__ __forceinline__ void cp_async16(bool issue, void* sdst, const void* gsrc, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
   const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(n)
-               : "memory");
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
+      "@p cp.async.cg.shared.global [%0], [%1], 16, %2;\n\t}" ::"r"(d),
+      "l"(gsrc), "r"(n), "r"((int)issue)
+      : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
@@ -380,22 +385,27 @@ __device__ __forceinline__ void cp_async_wait() {
 template <class T>
 __device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T* h, const T* M,
                                           const T* N, const T* emax, const float* man,
-                                          int rowbase, int pitch, int x0, int lane) {
+                                          int rowbase, int pitch, int x0, int lane, bool row_ok) {
   constexpr int E = 16 / (int)sizeof(T);  // elements per chunk
-  if (lane < kRingW / E) {
-    const int k = lane * E;
+  constexpr int NC = kRingW / E;          // chunks per row of a state array
+  static_assert(NC <= 32, "one chunk per lane");
+  {
+    const bool issue = row_ok && lane < NC;
+    const int k = (lane < NC ? lane : NC - 1) * E;
     const bool ok = x0 + k + E <= pitch;  // the chunk lies inside the allocated row
     const int g = ok ? rowbase + k : rowbase;
-    cp_async16(&S.e[k], eta + g, ok);
-    cp_async16(&S.h[k], h + g, ok);
-    cp_async16(&S.m[k], M + g, ok);
-    cp_async16(&S.nn[k], N + g + pitch, ok);
-    cp_async16(&S.em[k], emax + g, ok);
+    cp_async16(issue, &S.e[k], eta + g, ok);
+    cp_async16(issue, &S.h[k], h + g, ok);
+    cp_async16(issue, &S.m[k], M + g, ok);
+    cp_async16(issue, &S.nn[k], N + g + pitch, ok);
+    cp_async16(issue, &S.em[k], emax + g, ok);
   }
-  if (lane < kRingW / 4) {
-    const int k = lane * 4;
+  {
+    constexpr int NM = kRingW / 4;  // Manning n is binary32
+    const bool issue = row_ok && lane < NM;
+    const int k = (lane < NM ? lane : NM - 1) * 4;
     const bool ok = x0 + k + 4 <= pitch;
-    cp_async16(&S.nm[k], man + (ok ? rowbase + k : rowbase), ok);
+    cp_async16(issue, &S.nm[k], man + (ok ? rowbase + k : rowbase), ok);
   }
 }
 
@@ -638,9 +648,8 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   const int x0 = td.x0;
   int rowbase = (y0 - 2 + kYOff) * pitch + x0;
   for (int k = 0; k < kRingD - 1; ++k) {
-    if (y0 - 2 + k <= ye)
-      stage_row(ws.ring[k], etaP, hh, Mp, Np, emax, man, rowbase + k * pitch, pitch, x0,
-                lane);
+    stage_row(ws.ring[k], etaP, hh, Mp, Np, emax, man, rowbase + k * pitch, pitch, x0, lane,
+              y0 - 2 + k <= ye);
     cp_async_commit();
   }
   Row<T> A = {}, B = {}, C = {};
@@ -772,9 +781,8 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   int slot = 0;  // ring slot of row r
   for (int r = y0 - 2; r <= ye; ++r) {
     __syncwarp();  // every lane has read the slot of row r - 1 before it is refilled
-    if (r + kRingD - 1 <= ye)
-      stage_row(ws.ring[slot == 0 ? kRingD - 1 : slot - 1], etaP, hh, Mp, Np, emax, man,
-                rowbase + (kRingD - 1) * pitch, pitch, x0, lane);
+    stage_row(ws.ring[slot == 0 ? kRingD - 1 : slot - 1], etaP, hh, Mp, Np, emax, man,
+              rowbase + (kRingD - 1) * pitch, pitch, x0, lane, r + kRingD - 1 <= ye);
     cp_async_commit();
     cp_async_wait<kRingD - 1>();  // row r has landed
     __syncwarp();                 // ... for every lane's chunks
