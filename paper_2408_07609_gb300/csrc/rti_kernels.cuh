@@ -338,7 +338,8 @@ struct Row {
   T mb;          // M-bar of y-face (c, r)
   T SY, TY;      // N^2/D and N M-bar/D of y-face (c, r)
   float nm;      // Manning n of cell (c, r)
-  bool vx, vy;   // x-/y-face (c, r) is interior with D > dry_eps (usable by advection)
+  unsigned fl;   // bit 0: x-face (c, r), bit 1: y-face (c, r) is interior with D > dry_eps
+                 // (usable by advection)
 };
 
 // Raw inputs of row r: eta^n, h, M^n, eta_max, Manning n of (c, r); N^n of y-face (c, r+1).
@@ -701,10 +702,11 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     // ---- advective face terms of row r
     Nw.eL = __shfl_up_sync(full, e, 1);
     Nw.hL = __shfl_up_sync(full, Nw.H, 1);
+    unsigned fx;
     {  // x-face (c, r)
       const T dep = T(0.5) * (Nw.hL + Nw.H) + T(0.5) * (Nw.eL + Nw.E);
       const bool in = col_x && rin_x;
-      Nw.vx = in && dep > eps;
+      fx = (in && dep > eps) ? 1u : 0u;
       Nw.nb = T(0.25) * ((nSL + nS) + (nnL + nn));
       // Binary32 divides everywhere: a face without a usable depth gets a value that
       // every reader masks (usable flags) or discards (no wet pair on its own face).
@@ -716,7 +718,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     {  // y-face (c, r)
       const T dep = T(0.5) * (Z.H + Nw.H) + T(0.5) * (Z.E + Nw.E);
       const bool in = col_y && rin_y;
-      Nw.vy = in && dep > eps;
+      Nw.fl = fx | ((in && dep > eps) ? 2u : 0u);
       Nw.mb = T(0.25) * ((Z.MX + m) + (Z.mE + Nw.mE));
       T sy = T(0), ty = T(0);
       if (Ar<T>::kSelect || (in && dep != T(0))) Ar<T>::quot2(nS * nS, nS * Nw.mb, dep, sy, ty);
@@ -742,18 +744,19 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
         // open water for the whole warp: the faces of lanes 1..30 (the owned lanes and
         // their neighbours) are usable and every owned face has wet cells on both sides
         const bool open = lane == 0 || lane == 31 ||
-                          (Z.vx && Z.vy && (!own_col || (wW && wB && wA && Y.vx && X.vx &&
-                                                         Y.vy && X.vy)));
+                          (Z.fl == 3u && (!own_col || (wW && wB && wA && (Y.fl & X.fl) == 3u)));
         if (__all_sync(full, open)) {
           xm = mom_open(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, qm, Z.QX, qp, Y.RX, Z.RX, X.RX, nmL,
                         Z.nm, K);
           ym = mom_open(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.SY, Z.SY, X.SY, tw, Z.TY, te, Y.nm,
                         Z.nm, K);
         } else {
-          const unsigned bx = __ballot_sync(full, Z.vx), by = __ballot_sync(full, Z.vy);
+          const unsigned bx = __ballot_sync(full, Z.fl & 1u), by = __ballot_sync(full, Z.fl & 2u);
           xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, ((bx >> sl) & 1u) != 0, qm, Z.QX,
-                      ((bx >> sr) & 1u) != 0, qp, Y.vx, Y.RX, Z.RX, X.vx, X.RX, nmL, Z.nm, K);
-          ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.vy, Y.SY, Z.SY, X.vy, X.SY,
+                      ((bx >> sr) & 1u) != 0, qp, (Y.fl & 1u) != 0, Y.RX, Z.RX, (X.fl & 1u) != 0,
+                      X.RX, nmL, Z.nm, K);
+          ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, (Y.fl & 2u) != 0, Y.SY, Z.SY,
+                      (X.fl & 2u) != 0, X.SY,
                       ((by >> sl) & 1u) != 0, tw, Z.TY, ((by >> sr) & 1u) != 0, te, Y.nm, Z.nm,
                       K);
         }
