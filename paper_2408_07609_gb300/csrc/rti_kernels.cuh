@@ -383,31 +383,41 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Lanes issue the 16-byte chunks of row r (element `rowbase` = (r + 2) pitch + x0 is the
 // strip's column x0 - 4; N is taken one row up).
+// What a lane copies of every staged row (fixed for a strip): chunk k of the state
+// arrays and of Manning n, whether it has one, and whether it lies inside the row.
+struct StageLane {
+  int ke, km;
+  bool ie, oe, im, om;
+};
+template <class T>
+__device__ __forceinline__ StageLane stage_lane(int lane, int x0, int pitch) {
+  constexpr int E = 16 / (int)sizeof(T);  // elements per chunk
+  constexpr int NC = kRingW / E;          // chunks per row of a state array
+  constexpr int NM = kRingW / 4;          // chunks of Manning n (binary32)
+  static_assert(NC <= 32, "one chunk per lane");
+  StageLane L;
+  L.ie = lane < NC;
+  L.ke = (L.ie ? lane : NC - 1) * E;
+  L.oe = x0 + L.ke + E <= pitch;
+  L.im = lane < NM;
+  L.km = (L.im ? lane : NM - 1) * 4;
+  L.om = x0 + L.km + 4 <= pitch;
+  return L;
+}
+
 template <class T>
 __device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T* h, const T* M,
                                           const T* N, const T* emax, const float* man,
-                                          int rowbase, int pitch, int x0, int lane, bool row_ok) {
-  constexpr int E = 16 / (int)sizeof(T);  // elements per chunk
-  constexpr int NC = kRingW / E;          // chunks per row of a state array
-  static_assert(NC <= 32, "one chunk per lane");
-  {
-    const bool issue = row_ok && lane < NC;
-    const int k = (lane < NC ? lane : NC - 1) * E;
-    const bool ok = x0 + k + E <= pitch;  // the chunk lies inside the allocated row
-    const int g = ok ? rowbase + k : rowbase;
-    cp_async16(issue, &S.e[k], eta + g, ok);
-    cp_async16(issue, &S.h[k], h + g, ok);
-    cp_async16(issue, &S.m[k], M + g, ok);
-    cp_async16(issue, &S.nn[k], N + g + pitch, ok);
-    cp_async16(issue, &S.em[k], emax + g, ok);
-  }
-  {
-    constexpr int NM = kRingW / 4;  // Manning n is binary32
-    const bool issue = row_ok && lane < NM;
-    const int k = (lane < NM ? lane : NM - 1) * 4;
-    const bool ok = x0 + k + 4 <= pitch;
-    cp_async16(issue, &S.nm[k], man + (ok ? rowbase + k : rowbase), ok);
-  }
+                                          int rowbase, int pitch, const StageLane& L,
+                                          bool row_ok) {
+  const bool ie = row_ok && L.ie;
+  const int g = L.oe ? rowbase + L.ke : rowbase;
+  cp_async16(ie, &S.e[L.ke], eta + g, L.oe);
+  cp_async16(ie, &S.h[L.ke], h + g, L.oe);
+  cp_async16(ie, &S.m[L.ke], M + g, L.oe);
+  cp_async16(ie, &S.nn[L.ke], N + g + pitch, L.oe);
+  cp_async16(ie, &S.em[L.ke], emax + g, L.oe);
+  cp_async16(row_ok && L.im, &S.nm[L.km], man + (L.om ? rowbase + L.km : rowbase), L.om);
 }
 
 template <class T>
@@ -648,8 +658,9 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   T nSL = __shfl_up_sync(full, nS, 1);
   const int x0 = td.x0;
   int rowbase = (y0 - 2 + kYOff) * pitch + x0;
+  const StageLane SL = stage_lane<T>(lane, x0, pitch);
   for (int k = 0; k < kRingD - 1; ++k) {
-    stage_row(ws.ring[k], etaP, hh, Mp, Np, emax, man, rowbase + k * pitch, pitch, x0, lane,
+    stage_row(ws.ring[k], etaP, hh, Mp, Np, emax, man, rowbase + k * pitch, pitch, SL,
               y0 - 2 + k <= ye);
     cp_async_commit();
   }
@@ -785,7 +796,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   for (int r = y0 - 2; r <= ye; ++r) {
     __syncwarp();  // every lane has read the slot of row r - 1 before it is refilled
     stage_row(ws.ring[slot == 0 ? kRingD - 1 : slot - 1], etaP, hh, Mp, Np, emax, man,
-              rowbase + (kRingD - 1) * pitch, pitch, x0, lane, r + kRingD - 1 <= ye);
+              rowbase + (kRingD - 1) * pitch, pitch, SL, r + kRingD - 1 <= ye);
     cp_async_commit();
     cp_async_wait<kRingD - 1>();  // row r has landed
     __syncwarp();                 // ... for every lane's chunks
