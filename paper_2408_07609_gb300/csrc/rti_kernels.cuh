@@ -351,9 +351,11 @@ struct Raw {
 
 // The march's input rows are staged ahead in shared memory: a ring of kRingD slots per
 // warp, each holding elements [x0 - 4, x0 + 32) of the six input rows of one row r.
-// 16-byte cp.async.cg copies (through L2, no registers held) keep kRingD - 1 rows per
-// warp in flight. A copy that would start past the allocated row is a zero fill.
-constexpr int kRingD = 6;
+// 16-byte cp.async.cg copies (through L2, no registers held) keep kRingD - 2 rows per
+// warp in flight; a slot is refilled two rows after it was read, so one __syncwarp per
+// row orders the reads before the refill. A copy that would start past the allocated
+// row is a zero fill.
+constexpr int kRingD = 7;
 constexpr int kRingW = 36;
 
 template <class T>
@@ -659,7 +661,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   const int x0 = td.x0;
   int rowbase = (y0 - 2 + kYOff) * pitch + x0;
   const StageLane SL = stage_lane<T>(lane, x0, pitch);
-  for (int k = 0; k < kRingD - 1; ++k) {
+  for (int k = 0; k < kRingD - 2; ++k) {
     stage_row(ws.ring[k], etaP, hh, Mp, Np, emax, man, rowbase + k * pitch, pitch, SL,
               y0 - 2 + k <= ye);
     cp_async_commit();
@@ -747,30 +749,30 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
       // one whose owned faces are all in open water takes the short form
       const bool wA = Y.H + Y.E > eps, wB = Z.H + Z.E > eps, wW = Z.hL + Z.eL > eps;
       const bool act = own_col && (wW || wB || wA);
+      // open water for the whole warp: the faces of lanes 1..30 (the owned lanes and
+      // their neighbours) are usable and every owned face has wet cells on both sides
+      const bool open = lane == 0 || lane == 31 ||
+                        (Z.fl == 3u && (!own_col || (wW && wB && wA && (Y.fl & X.fl) == 3u)));
       T xm = T(0), ym = T(0);
-      if (__any_sync(full, act)) {
+      if (__all_sync(full, open)) {
         const T qm = __shfl_up_sync(full, Z.QX, 1), qp = __shfl_down_sync(full, Z.QX, 1);
         const T tw = __shfl_up_sync(full, Z.TY, 1), te = __shfl_down_sync(full, Z.TY, 1);
         const float nmL = __shfl_up_sync(full, Z.nm, 1);
-        // open water for the whole warp: the faces of lanes 1..30 (the owned lanes and
-        // their neighbours) are usable and every owned face has wet cells on both sides
-        const bool open = lane == 0 || lane == 31 ||
-                          (Z.fl == 3u && (!own_col || (wW && wB && wA && (Y.fl & X.fl) == 3u)));
-        if (__all_sync(full, open)) {
-          xm = mom_open(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, qm, Z.QX, qp, Y.RX, Z.RX, X.RX, nmL,
-                        Z.nm, K);
-          ym = mom_open(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.SY, Z.SY, X.SY, tw, Z.TY, te, Y.nm,
-                        Z.nm, K);
-        } else {
-          const unsigned bx = __ballot_sync(full, Z.fl & 1u), by = __ballot_sync(full, Z.fl & 2u);
-          xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, ((bx >> sl) & 1u) != 0, qm, Z.QX,
-                      ((bx >> sr) & 1u) != 0, qp, (Y.fl & 1u) != 0, Y.RX, Z.RX, (X.fl & 1u) != 0,
-                      X.RX, nmL, Z.nm, K);
-          ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, (Y.fl & 2u) != 0, Y.SY, Z.SY,
-                      (X.fl & 2u) != 0, X.SY,
-                      ((by >> sl) & 1u) != 0, tw, Z.TY, ((by >> sr) & 1u) != 0, te, Y.nm, Z.nm,
-                      K);
-        }
+        xm = mom_open(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, qm, Z.QX, qp, Y.RX, Z.RX, X.RX, nmL,
+                      Z.nm, K);
+        ym = mom_open(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.SY, Z.SY, X.SY, tw, Z.TY, te, Y.nm,
+                      Z.nm, K);
+      } else if (__any_sync(full, act)) {
+        const T qm = __shfl_up_sync(full, Z.QX, 1), qp = __shfl_down_sync(full, Z.QX, 1);
+        const T tw = __shfl_up_sync(full, Z.TY, 1), te = __shfl_down_sync(full, Z.TY, 1);
+        const float nmL = __shfl_up_sync(full, Z.nm, 1);
+        const unsigned bx = __ballot_sync(full, Z.fl & 1u), by = __ballot_sync(full, Z.fl & 2u);
+        xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, ((bx >> sl) & 1u) != 0, qm, Z.QX,
+                    ((bx >> sr) & 1u) != 0, qp, (Y.fl & 1u) != 0, Y.RX, Z.RX, (X.fl & 1u) != 0,
+                    X.RX, nmL, Z.nm, K);
+        ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, (Y.fl & 2u) != 0, Y.SY, Z.SY,
+                    (X.fl & 2u) != 0, X.SY, ((by >> sl) & 1u) != 0, tw, Z.TY,
+                    ((by >> sr) & 1u) != 0, te, Y.nm, Z.nm, K);
       }
       if (!edge_strip) {  // interior strip: every owned face is an interior face
         if (own_col) {
@@ -794,11 +796,11 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
 
   int slot = 0;  // ring slot of row r
   for (int r = y0 - 2; r <= ye; ++r) {
-    __syncwarp();  // every lane has read the slot of row r - 1 before it is refilled
-    stage_row(ws.ring[slot == 0 ? kRingD - 1 : slot - 1], etaP, hh, Mp, Np, emax, man,
-              rowbase + (kRingD - 1) * pitch, pitch, SL, r + kRingD - 1 <= ye);
+    // refill the slot of row r - 2: every lane read it before the __syncwarp of row r - 1
+    stage_row(ws.ring[slot >= 2 ? slot - 2 : slot + kRingD - 2], etaP, hh, Mp, Np, emax, man,
+              rowbase + (kRingD - 2) * pitch, pitch, SL, r + kRingD - 2 <= ye);
     cp_async_commit();
-    cp_async_wait<kRingD - 1>();  // row r has landed
+    cp_async_wait<kRingD - 2>();  // row r has landed
     __syncwarp();                 // ... for every lane's chunks
     const Raw<T> cur = read_row(ws.ring[slot], lane);
     slot = slot + 1 == kRingD ? 0 : slot + 1;
