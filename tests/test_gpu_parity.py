@@ -211,3 +211,65 @@ def test_never_wet_cells_report_nan_height_in_both_precisions(rti, oracle_mod):
         h.step(sc.steps)
         assert np.array_equal(np.isnan(h.max_height(0)), never)
         assert np.all(h.max_depth(0)[never] == 0.0)
+
+
+def _grid_scenario(name, blocks, dt, steps, seed=0):
+    """Flat 50 m sea with a land corner (wet/dry) on every block and a seeded Gaussian
+    bump on the root; block coordinates follow the 1:3 nesting."""
+    rng = np.random.default_rng(seed)
+    bathy, manning, uplift, origin = [], [], [], []
+    for k, b in enumerate(blocks):
+        if b["parent"] < 0:
+            x0 = y0 = 0.0
+        else:
+            P, (px, py) = blocks[b["parent"]], origin[b["parent"]]
+            x0, y0 = px + b["i0"] * P["dx"], py + b["j0"] * P["dx"]
+        origin.append((x0, y0))
+        x = x0 + (np.arange(b["nx"]) + 0.5) * b["dx"]
+        y = y0 + (np.arange(b["ny"]) + 0.5) * b["dx"]
+        X, Y = np.meshgrid(x, y)
+        h = np.full((b["ny"], b["nx"]), 50.0) + rng.uniform(-1, 1, (b["ny"], b["nx"]))
+        land = (X > x0 + 0.8 * b["nx"] * b["dx"]) & (Y > y0 + 0.8 * b["ny"] * b["dx"])
+        h[land] = -2.0
+        bathy.append(h)
+        manning.append(np.where(h > 0, 0.025, 0.04).astype(np.float32))
+        uplift.append(None)
+    R = blocks[0]
+    Lx, Ly = R["nx"] * R["dx"], R["ny"] * R["dx"]
+    xr = (np.arange(R["nx"]) + 0.5) * R["dx"]
+    yr = (np.arange(R["ny"]) + 0.5) * R["dx"]
+    Xr, Yr = np.meshgrid(xr, yr)
+    sig = max(R["dx"], 0.15 * min(Lx, Ly))
+    uplift[0] = 1.5 * np.exp(-((Xr - 0.4 * Lx) ** 2 + (Yr - 0.45 * Ly) ** 2) / (2 * sig**2))
+    return S.Scenario(name=name, blocks=blocks, bathy=bathy, manning=manning, uplift=uplift,
+                      dt=dt, steps=steps)
+
+
+def _root(nx, ny, dx=100.0, bc=(1, 1, 1, 1)):
+    return dict(level=1, parent=-1, nx=nx, ny=ny, i0=0, j0=0, dx=dx, bc=bc)
+
+
+@pytest.mark.parametrize("shape", [(3, 3), (5, 300), (300, 5), (28, 64), (29, 65), (57, 3)])
+def test_degenerate_single_grids_fp64(rti, oracle_mod, shape):
+    """Grids of the minimum size, thinner than a strip, exactly one strip, and one cell
+    past it: every strip is an edge strip and halo lanes fall outside the block."""
+    nx, ny = shape
+    sc = _grid_scenario(f"grid {nx}x{ny}", [_root(nx, ny)], dt=1.0, steps=150, seed=nx * ny)
+    for sched in (0, 1):
+        h, o = run_pair(rti, oracle_mod, sc, sc.steps, schedule=sched)
+        compare_fp64(h, o, 1)
+        h.close()
+        o.close()
+
+
+def test_smallest_children_fp64(rti, oracle_mod):
+    """A child of 3 x 3 cells (one parent cell, whose ring is itself), a 6 x 9 child and a
+    grandchild of 3 x 3 inside it, each at the 3-cell margin of its parent."""
+    blocks = [_root(40, 36, dx=300.0),
+              dict(level=2, parent=0, nx=3, ny=3, i0=3, j0=3, dx=100.0, bc=(0, 0, 0, 0)),
+              dict(level=2, parent=0, nx=15, ny=18, i0=30, j0=27, dx=100.0, bc=(0, 0, 0, 0)),
+              dict(level=3, parent=2, nx=3, ny=3, i0=3, j0=3, dx=100.0 / 3, bc=(0, 0, 0, 0))]
+    sc = _grid_scenario("smallest children", blocks, dt=0.5, steps=200, seed=7)
+    h, o = run_pair(rti, oracle_mod, sc, sc.steps)
+    compare_fp64(h, o, len(blocks))
+    assert max(abs(o.budget(k)["ring"]) for k in range(2)) > 0
