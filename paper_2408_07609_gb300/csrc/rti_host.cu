@@ -34,6 +34,8 @@ static thread_local std::string t_create_err;
 namespace {
 
 constexpr int kDefaultTx = kStripW, kDefaultTy = 64;
+// grid of the host-transfer kernels: 8 CTAs of 256 per SM of 152
+constexpr int kIoThreads = 256, kIoBlocks = 1216;
 constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at the maximum SM clock
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -50,7 +52,7 @@ size_t esize(int prec) { return prec == RTI_FP32 ? 4 : 8; }
 
 // Layout of one handle's arena; returns the total size.
 size_t plan_layout(const rti_block* b, int nb, int prec, int tx, int ty, std::vector<BlkMem>* mem,
-                   size_t* off_status) {
+                   size_t* off_status, size_t* off_io = nullptr) {
   size_t off = 0;
   const size_t es = esize(prec);
   if (mem) mem->resize(nb);
@@ -82,6 +84,12 @@ size_t plan_layout(const rti_block* b, int nb, int prec, int tx, int ty, std::ve
   size_t st = off;
   off = align256(off + 64);
   if (off_status) *off_status = st;
+  // binary64 staging of host reads and writes: one dense plane of the largest block
+  size_t io_elems = kIoBlocks;  // at least the partial sums of plane_sum
+  for (int k = 0; k < nb; ++k)
+    io_elems = std::max(io_elems, (size_t)(b[k].nx + 1) * (size_t)(b[k].ny + 1));
+  if (off_io) *off_io = off;
+  off = align256(off + io_elems * sizeof(double));
   return off;
 }
 
@@ -189,6 +197,7 @@ struct rti_handle {
   size_t arena_bytes = 0;
   bool own = false;
   size_t off_status = 0;
+  size_t off_io = 0;   // binary64 staging plane for host reads and writes
   long long base = 0;  // steps completed including enqueued work
   std::string err;
   rti_batch* batch = nullptr;
@@ -541,40 +550,162 @@ int read_status(Group* g, rti_handle* h, std::string* err) {
 
 bool bad_block(const rti_handle* h, int k) { return !h || k < 0 || k >= (int)h->blocks.size(); }
 
-// download a pitched plane (ncols x nrows starting at column/row 0) into a host double array
-int download(rti_handle* h, size_t off, int ncols, int nrows, int pitch, bool is_state,
-             double* out, std::string* err) {
-  const size_t es = is_state ? esize(h->prec) : 4;
-  std::vector<char> tmp((size_t)ncols * nrows * es);
-  const char* src = h->arena + off + ((size_t)kYOff * pitch + kXOff) * es;
-  cudaError_t e = cudaMemcpy2D(tmp.data(), (size_t)ncols * es, src, (size_t)pitch * es,
-                               (size_t)ncols * es, (size_t)nrows, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_err(err, e, "download");
-  h->d2h += (long long)tmp.size();
-  const size_t n = (size_t)ncols * nrows;
-  if (es == 8) std::memcpy(out, tmp.data(), n * 8);
-  else
-    for (size_t c = 0; c < n; ++c) out[c] = (double)((const float*)tmp.data())[c];
-  return RTI_OK;
+// ---- host transfers: binary64 host arrays <-> pitched planes in the state precision.
+// A host array is copied whole into the handle's binary64 staging plane, and a kernel
+// converts it into (or out of) the pitched layout, so the host does no per-cell work.
+
+template <class T>
+__global__ void k_plane_from_dense(const double* in, T* plane, int nx, int ny, int pitch) {
+  const long long n = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / nx), c = (int)(i - (long long)r * nx);
+    plane[(size_t)(r + kYOff) * pitch + (c + kXOff)] = (T)in[i];
+  }
 }
 
 template <class T>
-int upload_t(rti_handle* h, size_t off, int ncols, int nrows, int pitch, const double* in,
-             std::string* err) {
-  std::vector<T> tmp((size_t)ncols * nrows);
-  for (size_t c = 0; c < tmp.size(); ++c) tmp[c] = (T)in[c];
-  char* dst = h->arena + off + ((size_t)kYOff * pitch + kXOff) * sizeof(T);
-  cudaError_t e = cudaMemcpy2D(dst, (size_t)pitch * sizeof(T), tmp.data(), (size_t)ncols * sizeof(T),
-                               (size_t)ncols * sizeof(T), (size_t)nrows, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_err(err, e, "upload");
-  h->h2d += (long long)(tmp.size() * sizeof(T));
+__global__ void k_dense_from_plane(const T* plane, int nx, int ny, int pitch, double* out) {
+  const long long n = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / nx), c = (int)(i - (long long)r * nx);
+    out[i] = (double)plane[(size_t)(r + kYOff) * pitch + (c + kXOff)];
+  }
+}
+
+// forecast outputs of a block: 0 max depth (0 where never wet), 1 max height (NaN where
+// never wet; the marker is kNeverWet rounded to the state precision, tested by range),
+// 2 arrival time in seconds (-1 where the level never reached the threshold)
+template <class T>
+__global__ void k_output(int kind, const T* emax, const T* hpl, const int* arr, int nx, int ny,
+                         int pitch, double dt, double* out) {
+  const long long n = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / nx), c = (int)(i - (long long)r * nx);
+    const size_t o = (size_t)(r + kYOff) * pitch + (c + kXOff);
+    if (kind == 2) {
+      const int a = arr[o];
+      out[i] = a < 0 ? -1.0 : (double)a * dt;
+    } else {
+      const double em = (double)emax[o];
+      const bool never = em < 0.5 * kNeverWet;
+      out[i] = kind == 1 ? (never ? nan("") : em) : (never ? 0.0 : (double)hpl[o] + em);
+    }
+  }
+}
+
+// Initial state of a block (R10): eta0 = dz on sea cells (h > 0), floored at -h; the dry
+// land level -h elsewhere; max eta and arrival step from the initial level.
+template <class T>
+__global__ void k_init_block(const double* dz, const T* hpl, T* eta, T* emax, int* arr, int nx,
+                             int ny, int pitch, T eps, T thr) {
+  const long long n = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / nx), c = (int)(i - (long long)r * nx);
+    const size_t o = (size_t)(r + kYOff) * pitch + (c + kXOff);
+    const double hh = (double)hpl[o];
+    double e0;
+    if (hh > 0) {
+      e0 = dz ? dz[i] : 0.0;
+      if (e0 < -hh) e0 = -hh;
+    } else {
+      e0 = -hh;
+    }
+    const T e = (T)e0, ht = (T)hh;
+    T em = (T)kNeverWet;
+    int a = -1;
+    if (ht + e > eps && e > em) {
+      if (em < thr && e >= thr) a = 0;
+      em = e;
+    }
+    eta[o] = e;
+    emax[o] = em;
+    arr[o] = a;
+  }
+}
+
+// binary64 sum of a block's plane in a fixed order: kIoBlocks partial sums, summed on the host
+template <class T>
+__global__ void k_sum_plane(const T* plane, int nx, int ny, int pitch, double* part) {
+  __shared__ double red[kIoThreads / 32];
+  const long long n = (long long)nx * ny;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / nx), c = (int)(i - (long long)r * nx);
+    acc += (double)plane[(size_t)(r + kYOff) * pitch + (c + kXOff)];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kIoThreads / 32; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+double* io_plane(rti_handle* h) { return reinterpret_cast<double*>(h->arena + h->off_io); }
+
+// download a pitched plane (ncols x nrows starting at column/row 0) into a host double array
+int download(rti_handle* h, size_t off, int ncols, int nrows, int pitch, bool is_state,
+             double* out, std::string* err) {
+  const size_t n = (size_t)ncols * nrows;
+  double* io = io_plane(h);
+  if (!is_state)
+    k_dense_from_plane<float><<<kIoBlocks, kIoThreads>>>((const float*)(h->arena + off), ncols,
+                                                          nrows, pitch, io);
+  else if (h->prec == RTI_FP32)
+    k_dense_from_plane<float><<<kIoBlocks, kIoThreads>>>((const float*)(h->arena + off), ncols,
+                                                          nrows, pitch, io);
+  else
+    k_dense_from_plane<double><<<kIoBlocks, kIoThreads>>>((const double*)(h->arena + off),
+                                                           ncols, nrows, pitch, io);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(out, io, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(err, e, "download");
+  h->d2h += (long long)(n * sizeof(double));
   return RTI_OK;
 }
 
 int upload(rti_handle* h, size_t off, int ncols, int nrows, int pitch, const double* in,
            std::string* err) {
-  return h->prec == RTI_FP32 ? upload_t<float>(h, off, ncols, nrows, pitch, in, err)
-                             : upload_t<double>(h, off, ncols, nrows, pitch, in, err);
+  const size_t n = (size_t)ncols * nrows;
+  double* io = io_plane(h);
+  cudaError_t e = cudaMemcpy(io, in, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    if (h->prec == RTI_FP32)
+      k_plane_from_dense<float><<<kIoBlocks, kIoThreads>>>(io, (float*)(h->arena + off), ncols,
+                                                            nrows, pitch);
+    else
+      k_plane_from_dense<double><<<kIoBlocks, kIoThreads>>>(io, (double*)(h->arena + off), ncols,
+                                                             nrows, pitch);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_err(err, e, "upload");
+  h->h2d += (long long)(n * sizeof(double));
+  return RTI_OK;
+}
+
+// binary64 sum of the state-precision plane at `off` (block k)
+int plane_sum(rti_handle* h, size_t off, int nx, int ny, int pitch, double* sum, std::string* err) {
+  double* io = io_plane(h);
+  if (h->prec == RTI_FP32)
+    k_sum_plane<float><<<kIoBlocks, kIoThreads>>>((const float*)(h->arena + off), nx, ny, pitch, io);
+  else
+    k_sum_plane<double><<<kIoBlocks, kIoThreads>>>((const double*)(h->arena + off), nx, ny, pitch,
+                                                    io);
+  std::vector<double> part(kIoBlocks);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(part.data(), io, kIoBlocks * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(err, e, "plane sum");
+  double t = 0.0;
+  for (double v : part) t += v;
+  *sum = t;
+  return RTI_OK;
 }
 
 int wait_handle(rti_handle* h) {
@@ -583,52 +714,26 @@ int wait_handle(rti_handle* h) {
   return RTI_OK;
 }
 
-// initial level and outputs of block k on the host, in the state precision
+// initial level and outputs of block k (dz: host binary64 uplift, or null for rest)
 template <class T>
-int init_block_t(rti_handle* h, int k, const double* dz, const double* host_h) {
+int init_block_t(rti_handle* h, int k, const double* dz) {
   const rti_block& d = h->blocks[k];
   const BlkMem& m = h->mem[k];
   const size_t n = (size_t)d.nx * d.ny;
-  std::vector<double> hd;
-  if (!host_h) {
-    hd.resize(n);
-    int rc = download(h, m.h, d.nx, d.ny, m.pitch, true, hd.data(), &h->err);
-    if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  double* io = io_plane(h);
+  if (dz) {
+    e = cudaMemcpy(io, dz, n * sizeof(double), cudaMemcpyHostToDevice);
+    h->h2d += (long long)(n * sizeof(double));
   }
-  const double* hsrc = host_h ? host_h : hd.data();
-  std::vector<T> eta(n), emax(n);
-  std::vector<int> arr(n);
-  const T eps = (T)h->params.dry_eps, thr = (T)h->params.arrival_thr;
-  for (size_t c = 0; c < n; ++c) {
-    const double hh = (double)(T)hsrc[c];
-    double e0;
-    if (hh > 0) {
-      e0 = dz ? dz[c] : 0.0;
-      if (e0 < -hh) e0 = -hh;
-    } else {
-      e0 = -hh;
-    }
-    T e = (T)e0;
-    const T ht = (T)hh;
-    eta[c] = e;
-    emax[c] = (T)kNeverWet;
-    arr[c] = -1;
-    if (ht + e > eps && e > emax[c]) {
-      if (emax[c] < thr && e >= thr) arr[c] = 0;
-      emax[c] = e;
-    }
+  if (e == cudaSuccess) {
+    k_init_block<T><<<kIoBlocks, kIoThreads>>>(
+        dz ? io : nullptr, (const T*)(h->arena + m.h), (T*)(h->arena + m.eta[0]),
+        (T*)(h->arena + m.emax), (int*)(h->arena + m.arr), d.nx, d.ny, m.pitch,
+        (T)h->params.dry_eps, (T)h->params.arrival_thr);
+    e = cudaGetLastError();
   }
-  const size_t es = sizeof(T);
-  auto put = [&](size_t off, const void* src, size_t el) -> cudaError_t {
-    char* dst = h->arena + off + ((size_t)kYOff * m.pitch + kXOff) * el;
-    h->h2d += (long long)(n * el);
-    return cudaMemcpy2D(dst, (size_t)m.pitch * el, src, (size_t)d.nx * el, (size_t)d.nx * el,
-                        (size_t)d.ny, cudaMemcpyHostToDevice);
-  };
-  const size_t plane = (size_t)m.pitch * m.rows;
-  cudaError_t e = put(m.eta[0], eta.data(), es);
-  if (e == cudaSuccess) e = put(m.emax, emax.data(), es);
-  if (e == cudaSuccess) e = put(m.arr, arr.data(), 4);
+  const size_t plane = (size_t)m.pitch * m.rows, es = sizeof(T);
   for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = cudaMemset(h->arena + m.M[s], 0, plane * es);
   for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = cudaMemset(h->arena + m.N[s], 0, plane * es);
   if (e == cudaSuccess)
@@ -699,7 +804,7 @@ int rti_create(const rti_block* blocks, int nblocks, const double* const* bathy,
   h->params.tile_y = params->tile_y ? params->tile_y : kDefaultTy;
   h->blocks.assign(blocks, blocks + nblocks);
   h->arena_bytes = plan_layout(blocks, nblocks, h->prec, h->params.tile_x, h->params.tile_y,
-                               &h->mem, &h->off_status);
+                               &h->mem, &h->off_status, &h->off_io);
   for (int k = 0; k < nblocks; ++k) h->cells += (long long)blocks[k].nx * blocks[k].ny;
   cudaError_t e = cudaSuccess;
   if (device_mem) {
@@ -741,10 +846,8 @@ int rti_create(const rti_block* blocks, int nblocks, const double* const* bathy,
     const size_t n = (size_t)d.nx * d.ny;
     rc = upload(h, m.h, d.nx, d.ny, m.pitch, bathy[k], &h->err);
     if (rc) return fail(rc);
-    double s = 0.0;
-    for (size_t c = 0; c < n; ++c)
-      s += h->prec == RTI_FP32 ? (double)(float)bathy[k][c] : bathy[k][c];
-    h->sum_h[k] = s;
+    rc = plane_sum(h, m.h, d.nx, d.ny, m.pitch, &h->sum_h[k], &h->err);
+    if (rc) return fail(rc);
     char* dst = h->arena + m.man + ((size_t)kYOff * m.pitch + kXOff) * 4;
     e = cudaMemcpy2D(dst, (size_t)m.pitch * 4, manning[k], (size_t)d.nx * 4, (size_t)d.nx * 4,
                      (size_t)d.ny, cudaMemcpyHostToDevice);
@@ -763,8 +866,8 @@ int rti_create(const rti_block* blocks, int nblocks, const double* const* bathy,
   rc = group_upload_any(h->self, 0, &h->err);
   if (rc) return fail(rc);
   for (int k = 0; k < nblocks; ++k) {
-    rc = h->prec == RTI_FP32 ? init_block_t<float>(h, k, nullptr, bathy[k])
-                             : init_block_t<double>(h, k, nullptr, bathy[k]);
+    rc = h->prec == RTI_FP32 ? init_block_t<float>(h, k, nullptr)
+                             : init_block_t<double>(h, k, nullptr);
     if (rc) return fail(rc);
   }
   rc = snapshot_any(h->self, 0, &h->err);
@@ -795,8 +898,8 @@ int rti_set_initial_uplift(rti_handle* h, int block, const double* dz) {
     }
   }
   h->base = 0;
-  rc = h->prec == RTI_FP32 ? init_block_t<float>(h, block, dz, nullptr)
-                           : init_block_t<double>(h, block, dz, nullptr);
+  rc = h->prec == RTI_FP32 ? init_block_t<float>(h, block, dz)
+                           : init_block_t<double>(h, block, dz);
   if (rc) return rc;
   cudaError_t e = cudaMemset(h->arena + h->off_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->self->d_status, 0, sizeof(int));
@@ -898,28 +1001,20 @@ static int get_out(rti_handle* h, int block, double* out, int kind) {
   const rti_block& d = h->blocks[block];
   const BlkMem& m = h->mem[block];
   const size_t n = (size_t)d.nx * d.ny;
-  if (kind == 2) {  // arrival
-    std::vector<int> a(n);
-    char* src = h->arena + m.arr + ((size_t)kYOff * m.pitch + kXOff) * 4;
-    cudaError_t e = cudaMemcpy2D(a.data(), (size_t)d.nx * 4, src, (size_t)m.pitch * 4,
-                                 (size_t)d.nx * 4, (size_t)d.ny, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_err(&h->err, e, "arrival");
-    h->d2h += (long long)n * 4;
-    for (size_t c = 0; c < n; ++c) out[c] = a[c] < 0 ? -1.0 : (double)a[c] * h->params.dt;
-    return RTI_OK;
-  }
-  std::vector<double> em(n);
-  rc = download(h, m.emax, d.nx, d.ny, m.pitch, true, em.data(), &h->err);
-  if (rc) return rc;
-  // the never-wet marker is kNeverWet rounded to the state precision: test by range
-  if (kind == 1) {  // max height
-    for (size_t c = 0; c < n; ++c) out[c] = em[c] < 0.5 * kNeverWet ? NAN : em[c];
-    return RTI_OK;
-  }
-  std::vector<double> hd(n);
-  rc = download(h, m.h, d.nx, d.ny, m.pitch, true, hd.data(), &h->err);
-  if (rc) return rc;
-  for (size_t c = 0; c < n; ++c) out[c] = em[c] < 0.5 * kNeverWet ? 0.0 : hd[c] + em[c];
+  double* io = io_plane(h);
+  const int* arr = (const int*)(h->arena + m.arr);
+  if (h->prec == RTI_FP32)
+    k_output<float><<<kIoBlocks, kIoThreads>>>(kind, (const float*)(h->arena + m.emax),
+                                                (const float*)(h->arena + m.h), arr, d.nx, d.ny,
+                                                m.pitch, h->params.dt, io);
+  else
+    k_output<double><<<kIoBlocks, kIoThreads>>>(kind, (const double*)(h->arena + m.emax),
+                                                 (const double*)(h->arena + m.h), arr, d.nx, d.ny,
+                                                 m.pitch, h->params.dt, io);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(out, io, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "outputs");
+  h->d2h += (long long)(n * sizeof(double));
   return RTI_OK;
 }
 
