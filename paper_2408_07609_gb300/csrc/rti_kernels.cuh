@@ -29,6 +29,7 @@
 
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "rti_layout.h"
@@ -355,7 +356,16 @@ struct Raw {
 // warp in flight; a slot is refilled two rows after it was read, so one __syncwarp per
 // row orders the reads before the refill. A copy that would start past the allocated
 // row is a zero fill.
-constexpr int kRingD = 7;
+// slots per warp, a power of two (slots are taken modulo by a mask): binary64 is bound by
+// its arithmetic and keeps fewer rows in flight, inside the 48 KB of static shared memory
+template <class T>
+struct RingD {
+  static constexpr int D = 8;
+};
+template <>
+struct RingD<double> {
+  static constexpr int D = 4;
+};
 constexpr int kRingW = 36;
 
 template <class T>
@@ -407,18 +417,36 @@ __device__ __forceinline__ StageLane stage_lane(int lane, int x0, int pitch) {
   return L;
 }
 
+// The five state-array chunks of a lane under one predicate: shared destinations kRingW
+// elements (STRIDE bytes) apart from `d`.
+template <int STRIDE>
+__device__ __forceinline__ void cp_async16x5(bool issue, unsigned d, const void* g0,
+                                             const void* g1, const void* g2, const void* g3,
+                                             const void* g4, bool valid) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+      "@p cp.async.cg.shared.global [%0], [%1], 16, %7;\n\t"
+      "@p cp.async.cg.shared.global [%0+%8], [%2], 16, %7;\n\t"
+      "@p cp.async.cg.shared.global [%0+%9], [%3], 16, %7;\n\t"
+      "@p cp.async.cg.shared.global [%0+%10], [%4], 16, %7;\n\t"
+      "@p cp.async.cg.shared.global [%0+%11], [%5], 16, %7;\n\t}" ::"r"(d),
+      "l"(g0), "l"(g1), "l"(g2), "l"(g3), "l"(g4), "r"((int)issue), "r"(valid ? 16 : 0),
+      "n"(STRIDE), "n"(2 * STRIDE), "n"(3 * STRIDE), "n"(4 * STRIDE)
+      : "memory");
+}
+
 template <class T>
 __device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T* h, const T* M,
                                           const T* N, const T* emax, const float* man,
                                           int rowbase, int pitch, const StageLane& L,
                                           bool row_ok) {
-  const bool ie = row_ok && L.ie;
+  static_assert(offsetof(RingSlot<T>, h) == kRingW * sizeof(T) &&
+                    offsetof(RingSlot<T>, em) == 4 * kRingW * sizeof(T),
+                "state rows kRingW elements apart");
   const int g = L.oe ? rowbase + L.ke : rowbase;
-  cp_async16(ie, &S.e[L.ke], eta + g, L.oe);
-  cp_async16(ie, &S.h[L.ke], h + g, L.oe);
-  cp_async16(ie, &S.m[L.ke], M + g, L.oe);
-  cp_async16(ie, &S.nn[L.ke], N + g + pitch, L.oe);
-  cp_async16(ie, &S.em[L.ke], emax + g, L.oe);
+  cp_async16x5<kRingW * (int)sizeof(T)>(row_ok && L.ie,
+                                        (unsigned)__cvta_generic_to_shared(&S.e[L.ke]), eta + g,
+                                        h + g, M + g, N + g + pitch, emax + g, L.oe);
   cp_async16(row_ok && L.im, &S.nm[L.km], man + (L.om ? rowbase + L.km : rowbase), L.om);
 }
 
@@ -514,7 +542,7 @@ __device__ __forceinline__ T radiate_r(T h, T e, T sign, T eps, T g) {
 // scenario counters and the index of the block staged.
 template <class T>
 struct WarpSlot {
-  RingSlot<T> ring[kRingD];
+  RingSlot<T> ring[RingD<T>::D];
   Blk<T> b;
   Blk<T> P;
   ScenDev sc;
@@ -618,6 +646,7 @@ __device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<
 template <class T>
 __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& ws, Tile td,
                                             int s) {
+  constexpr int kRingD = RingD<T>::D;
   const int lane = threadIdx.x;
   const Blk<T>& b = ws.b;
   const ScenDev sc = ws.sc;
@@ -655,7 +684,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   // element offsets within a plane fit in 32 bits (rti_create checks pitch x rows < 2^31)
   int o = (y0 - 2 + kYOff) * pitch + (c + kXOff);
 
-  // prologue: N^n of y-face (c, y0 - 2); rows y0 - 2 .. y0 + kRingD - 4 staged
+  // prologue: N^n of y-face (c, y0 - 2); rows y0 - 2 .. y0 + kRingD - 5 staged
   T nS = col_ok ? __ldcg(Np + o) : T(0);  // y0 - 2 is below row 0 or an interior row
   T nSL = __shfl_up_sync(full, nS, 1);
   const int x0 = td.x0;
@@ -797,13 +826,13 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   int slot = 0;  // ring slot of row r
   for (int r = y0 - 2; r <= ye; ++r) {
     // refill the slot of row r - 2: every lane read it before the __syncwarp of row r - 1
-    stage_row(ws.ring[slot >= 2 ? slot - 2 : slot + kRingD - 2], etaP, hh, Mp, Np, emax, man,
+    stage_row(ws.ring[(slot - 2) & (kRingD - 1)], etaP, hh, Mp, Np, emax, man,
               rowbase + (kRingD - 2) * pitch, pitch, SL, r + kRingD - 2 <= ye);
     cp_async_commit();
     cp_async_wait<kRingD - 2>();  // row r has landed
     __syncwarp();                 // ... for every lane's chunks
     const Raw<T> cur = read_row(ws.ring[slot], lane);
-    slot = slot + 1 == kRingD ? 0 : slot + 1;
+    slot = (slot + 1) & (kRingD - 1);
     rowbase += pitch;
     Row<T> X;
     row(cur, X, B, C, r);
