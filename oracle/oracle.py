@@ -67,7 +67,8 @@ def lib(path=None):
         L.orc_steps_done.restype = C.c_long
         for name in ("orc_get_state", "orc_set_state"):
             getattr(L, name).argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
-        for name in ("orc_get_max_height", "orc_get_max_depth", "orc_get_arrival_time",
+        for name in ("orc_get_max_height", "orc_get_max_depth", "orc_get_max_velocity",
+                     "orc_get_arrival_time",
                      "orc_get_budget"):
             getattr(L, name).argtypes = [C.c_void_p, C.c_int, dp]
         _libs[key] = L
@@ -166,6 +167,9 @@ class Oracle:
 
     def max_height(self, k):
         return self._field("orc_get_max_height", k)
+
+    def max_velocity(self, k):
+        return self._field("orc_get_max_velocity", k)
 
     def max_depth(self, k):
         return self._field("orc_get_max_depth", k)

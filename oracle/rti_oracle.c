@@ -45,6 +45,12 @@
  *   R9  after R8: on wet cells, etamax = max(etamax, eta); the arrival step is recorded
  *       when etamax first reaches the threshold (>=).
  *   R10 initial state: eta0 = max(dz, -h) on sea cells, -h on land, fluxes zero.
+ *   R11 maximum water velocity (the output update of Sec. IV-A names it; no formula is
+ *       given): cell-centre speed of a state, u = (Mw + Me)/2 / D, v = (Ns + Nn)/2 / D with
+ *       D = h + eta, kept as its square (u^2 + v^2) / D^2 on wet cells (D > dry_eps). It is
+ *       taken from the state each step starts from (the state the previous iteration
+ *       finished with), and the read adds the current state, so the result is the maximum
+ *       over the initial state and every state a step finished with; 0 if never wet.
  */
 #include "rti_oracle.h"
 
@@ -67,7 +73,8 @@ typedef struct {
   double* N;    /* (ny+1)*nx */
   double* N1;
   double* emax;
-  long* arr; /* arrival step, -1 if never */
+  long* arr;     /* arrival step, -1 if never */
+  double* vmax2; /* R11: max squared cell-centre speed on wet instants (0 if never) */
   double outflow, clip, ring;
 } oblk;
 
@@ -85,7 +92,7 @@ struct orc_state {
 
 static void free_blk(oblk* b) {
   free(b->h); free(b->n); free(b->eta); free(b->eta1); free(b->M); free(b->M1);
-  free(b->N); free(b->N1); free(b->emax); free(b->arr);
+  free(b->N); free(b->N1); free(b->emax); free(b->arr); free(b->vmax2);
 }
 
 void orc_destroy(orc_state* s) {
@@ -166,8 +173,9 @@ orc_state* orc_create(const orc_block* blocks, int nblocks, const double* const*
     b->N1 = (double*)calloc(nfy, sizeof(double));
     b->emax = (double*)malloc(nc * sizeof(double));
     b->arr = (long*)malloc(nc * sizeof(long));
+    b->vmax2 = (double*)calloc(nc, sizeof(double));
     if (!b->h || !b->n || !b->eta || !b->eta1 || !b->M || !b->M1 || !b->N || !b->N1 ||
-        !b->emax || !b->arr)
+        !b->emax || !b->arr || !b->vmax2)
       goto oom;
     for (size_t c = 0; c < nc; ++c) {
       b->h[c] = bathy[k][c];
@@ -192,6 +200,25 @@ static void track_cell(oblk* b, size_t c, long step, const orc_params* p) {
   }
 }
 
+/* R11: squared cell-centre speed of cell (i, j) in the state (eta, M, N); -1 if dry */
+static double speed2(const oblk* b, const double* eta, const double* M, const double* N, int i,
+                     int j, const orc_params* p) {
+  double D = b->h[C(b, i, j)] + eta[C(b, i, j)];
+  if (!(D > p->dry_eps)) return -1.0;
+  double u = 0.5 * (M[FX(b, i, j)] + M[FX(b, i + 1, j)]);
+  double v = 0.5 * (N[FY(b, i, j)] + N[FY(b, i, j + 1)]);
+  return (u * u + v * v) / (D * D);
+}
+
+/* R11 output update: the state a step starts from */
+static void track_speed(oblk* b, const orc_params* p) {
+  for (int j = 0; j < b->ny; ++j)
+    for (int i = 0; i < b->nx; ++i) {
+      double s2 = speed2(b, b->eta, b->M, b->N, i, j, p);
+      if (s2 > b->vmax2[C(b, i, j)]) b->vmax2[C(b, i, j)] = s2;
+    }
+}
+
 /* R10 (dz == NULL: sea at rest) */
 int orc_set_initial_uplift(orc_state* s, int k, const double* dz) {
   if (!s || k < 0 || k >= s->nb) return ORC_ERR_INVALID_ARG;
@@ -210,6 +237,7 @@ int orc_set_initial_uplift(orc_state* s, int k, const double* dz) {
     b->eta1[c] = e;
     b->emax[c] = NEVER_WET;
     b->arr[c] = -1;
+    b->vmax2[c] = 0.0;
     track_cell(b, c, 0, &s->p);
   }
   memset(b->M, 0, (size_t)(b->nx + 1) * b->ny * sizeof(double));
@@ -505,6 +533,7 @@ int orc_step(orc_state* s, int nsteps) {
   if (!s || nsteps < 0) return ORC_ERR_INVALID_ARG;
   for (int it = 0; it < nsteps; ++it) {
     long step = s->step + 1;
+    for (int k = 0; k < s->nb; ++k) track_speed(&s->b[k], &s->p);
     for (int k = 0; k < s->nb; ++k) mass_block(&s->b[k], &s->p);
     for (int k = s->nb - 1; k >= 0; --k) /* finest first */
       if (s->b[k].d.parent >= 0) ring_child(s, k);
@@ -559,6 +588,19 @@ int orc_get_max_depth(const orc_state* s, int k, double* out) {
   const oblk* b = &s->b[k];
   for (size_t c = 0; c < (size_t)b->nx * b->ny; ++c)
     out[c] = b->emax[c] == NEVER_WET ? 0.0 : b->h[c] + b->emax[c];
+  return ORC_OK;
+}
+
+int orc_get_max_velocity(const orc_state* s, int k, double* out) {
+  if (!s || k < 0 || k >= s->nb || !out) return ORC_ERR_INVALID_ARG;
+  const oblk* b = &s->b[k];
+  for (int j = 0; j < b->ny; ++j)
+    for (int i = 0; i < b->nx; ++i) {
+      double m = b->vmax2[C(b, i, j)];
+      double s2 = speed2(b, b->eta, b->M, b->N, i, j, &s->p);
+      if (s2 > m) m = s2;
+      out[C(b, i, j)] = sqrt(m);
+    }
   return ORC_OK;
 }
 

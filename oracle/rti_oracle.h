@@ -69,6 +69,9 @@ int orc_get_max_height(const orc_state* s, int block, double* out);
 int orc_get_max_depth(const orc_state* s, int block, double* out);
 /* seconds, -1 if max eta never reached the threshold */
 int orc_get_arrival_time(const orc_state* s, int block, double* out);
+/* R11: max over the initial state and every finished step of the cell-centre speed
+ * sqrt(((Mw+Me)/2)^2 + ((Ns+Nn)/2)^2) / (h + eta) on wet cells, m/s (0 if never wet) */
+int orc_get_max_velocity(const orc_state* s, int block, double* out);
 /* out[0] = water volume sum (h+eta) dx^2, out[1] = cumulative volume that left through
  * the block boundary, out[2] = cumulative volume added by the dry clip, out[3] = cumulative
  * volume changed by the fine-to-coarse replacement of ring cells. */

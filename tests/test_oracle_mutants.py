@@ -38,11 +38,22 @@ MUTANTS = [
     ("outputs: strict arrival threshold", "e >= p->arrival_thr", "e > p->arrival_thr"),
     ("outputs: max tracked on dry cells", "if (b->h[c] + e > p->dry_eps && e > b->emax[c])",
      "if (e > b->emax[c])"),
+    ("velocity: west face only", "double u = 0.5 * (M[FX(b, i, j)] + M[FX(b, i + 1, j)]);",
+     "double u = M[FX(b, i, j)];"),
+    ("velocity: speed without the depth", "return (u * u + v * v) / (D * D);",
+     "return (u * u + v * v);"),
+    ("velocity: y faces of the wrong row", "double v = 0.5 * (N[FY(b, i, j)] + N[FY(b, i, j + 1)]);",
+     "double v = 0.5 * (N[FY(b, i, j)] + N[FY(b, i, j)]);"),
+    ("velocity: not a running maximum", "if (s2 > b->vmax2[C(b, i, j)]) b->vmax2[C(b, i, j)] = s2;",
+     "b->vmax2[C(b, i, j)] = s2 > 0 ? s2 : 0.0;"),
 ]
 
 # cheapest first; each takes the oracle module as its only argument
 BATTERY = [
     pins.test_cfl_and_nesting_rejected,
+    pins.test_max_velocity_averages_the_two_faces_of_a_cell,
+    pins.test_max_velocity_of_uniform_flow_is_exact,
+    pins.test_max_velocity_is_zero_at_rest_and_on_dry_land_and_grows_monotonically,
     pins.test_max_and_arrival_are_functions_of_history,
     pins.test_nest_constant_field_ring_average,
     pins.test_nest_edge_flux_reproduces_linear_profile,

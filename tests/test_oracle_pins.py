@@ -414,3 +414,70 @@ def test_cfl_and_nesting_rejected(oracle_mod):
     bad[1]["dx"] = 99.0
     with pytest.raises(oracle_mod.OracleError):
         oracle_mod.Oracle(bad, bathy, man, dt=2.0)
+
+
+# ---------------------------------------------------------------- R11 max velocity
+def _flat_basin(oracle_mod, nx=64, ny=64, h=8.0, n=0.0, dt=1.0, dx=100.0):
+    blk = dict(level=1, parent=-1, nx=nx, ny=ny, i0=0, j0=0, dx=dx, bc=(0, 0, 0, 0))
+    bathy = np.full((ny, nx), h)
+    man = np.full((ny, nx), n, np.float32)
+    return oracle_mod.Oracle([blk], [bathy], [man], dt)
+
+
+def test_max_velocity_of_uniform_flow_is_exact(oracle_mod):
+    """Uniform frictionless flow over a flat bottom is an exact steady solution away from
+    the walls: M = 4, N = 3 m^2/s on h = 8 m gives u = 1/2, v = 3/8 and a speed of exactly
+    5/8 m/s in every cell the walls have not yet reached (the scheme's stencil spreads
+    one cell per step)."""
+    o = _flat_basin(oracle_mod)
+    nx = ny = 64
+    M = np.full((ny, nx + 1), 4.0)
+    M[:, 0] = M[:, nx] = 0.0
+    N = np.full((ny + 1, nx), 3.0)
+    N[0, :] = N[ny, :] = 0.0
+    o.set_state(0, eta=np.zeros((ny, nx)), M=M, N=N)
+    o.step(10)
+    v = o.max_velocity(0)
+    core = v[20:44, 20:44]
+    assert np.all(core == 0.625)
+    e, M1, N1 = o.get_state(0)
+    assert np.all(M1[20:44, 20:44] == 4.0) and np.all(e[20:44, 20:44] == 0.0)
+
+
+def test_max_velocity_averages_the_two_faces_of_a_cell(oracle_mod):
+    """Flux fields linear in x and in y, M(f, j) = f / 4 and N(i, g) = g / 8, give the
+    cell-centre velocity ((i + 1/2) / 4, (j + 1/2) / 8) / h (closed form of the face
+    means): a shifted face index, a dropped 1/2 or a missing depth changes the values.
+    Read before any step, so only the current state counts."""
+    nx, ny, h = 16, 12, 2.0
+    o = _flat_basin(oracle_mod, nx=nx, ny=ny, h=h)
+    M = np.tile(np.arange(nx + 1, dtype=float) / 4.0, (ny, 1))
+    N = np.tile((np.arange(ny + 1, dtype=float) / 8.0)[:, None], (1, nx))
+    o.set_state(0, eta=np.zeros((ny, nx)), M=M, N=N)
+    u = np.tile((np.arange(nx) + 0.5) / 4.0, (ny, 1)) / h
+    v = np.tile(((np.arange(ny) + 0.5) / 8.0)[:, None], (1, nx)) / h
+    assert np.allclose(o.max_velocity(0), np.hypot(u, v), rtol=1e-15, atol=0)
+    # with N alone the speed is the y component, exactly
+    o.set_state(0, M=np.zeros((ny, nx + 1)))
+    assert np.array_equal(o.max_velocity(0), v)
+
+
+def test_max_velocity_is_zero_at_rest_and_on_dry_land_and_grows_monotonically(oracle_mod):
+    """Lake at rest: 0 everywhere. After a source: a running maximum (never decreases
+    between reads), positive where the wave passed, 0 on land that never got wet."""
+    from paper_2408_07609_gb300 import scenarios as S
+
+    sc = S.config1(nx=96, ny=64, steps=0)
+    o = oracle_mod.from_scenario(sc)
+    o.set_initial_uplift(0, np.zeros((64, 96)))
+    o.step(50)
+    assert np.all(o.max_velocity(0) == 0.0)  # lake at rest
+    o.set_initial_uplift(0, sc.uplift[0])
+    prev = o.max_velocity(0)
+    for _ in range(5):
+        o.step(40)
+        cur = o.max_velocity(0)
+        assert np.all(cur >= prev)
+        prev = cur
+    never_wet = np.isnan(o.max_height(0))
+    assert prev.max() > 0.01 and never_wet.any() and np.all(prev[never_wet] == 0.0)
