@@ -72,6 +72,8 @@ typedef struct {
   int tile_x;         /* strip width in cells: 0 or 28 (a warp's 32 lanes less a 2-cell halo
                          on each side); other values are RTI_ERR_INVALID_ARG */
   int tile_y;         /* strip height in cells, a multiple of 8; 0 = 64 */
+  int track_velocity; /* 1: keep the maximum water velocity (one more plane per block and a
+                         read of it per cell-step); 0: off. Not for rti_step_noalloc. */
 } rti_params;
 
 typedef struct rti_handle rti_handle;
@@ -110,6 +112,12 @@ int rti_sync(rti_handle* h);
 int rti_get_max_depth(rti_handle* h, int block, double* out);
 int rti_get_max_height(rti_handle* h, int block, double* out);
 int rti_get_arrival_time(rti_handle* h, int block, double* out);
+/* Maximum water velocity (Sec. IV-A names it among the outputs of the time loop; the
+ * formula is this library's reading): the largest cell-centre speed
+ * sqrt(((Mw + Me)/2)^2 + ((Ns + Nn)/2)^2) / (h + eta) over the initial state and every
+ * state a step finished with, on wet cells (h + eta > dry_eps), m/s, 0 if never wet.
+ * Needs track_velocity = 1 at create; otherwise RTI_ERR_STATE. */
+int rti_get_max_velocity(rti_handle* h, int block, double* out);
 
 /* Checkpoint access: current eta (nx*ny), M (ny*(nx+1)), N ((ny+1)*nx); NULL skips one.
  * rti_set_state leaves maxima, arrival, budget terms and the step counter unchanged. */

@@ -43,6 +43,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct BlkMem {
   size_t eta[2], M[2], N[2], h, emax, man, arr, budget;
   size_t ring;  // fine-to-coarse overrides of a block with children (0 = none)
+  size_t vmax;  // running max of the squared speed (0 = not tracked)
   int pitch;
   long long rows;
   int tiles_x, tiles_y;
@@ -52,7 +53,7 @@ size_t esize(int prec) { return prec == RTI_FP32 ? 4 : 8; }
 
 // Layout of one handle's arena; returns the total size.
 size_t plan_layout(const rti_block* b, int nb, int prec, int tx, int ty, std::vector<BlkMem>* mem,
-                   size_t* off_status, size_t* off_io = nullptr) {
+                   size_t* off_status, size_t* off_io = nullptr, bool velocity = false) {
   size_t off = 0;
   const size_t es = esize(prec);
   if (mem) mem->resize(nb);
@@ -76,6 +77,7 @@ size_t plan_layout(const rti_block* b, int nb, int prec, int tx, int ty, std::ve
     bool parent_of_some = false;
     for (int c = 0; c < nb; ++c) parent_of_some |= b[c].parent == k;
     m.ring = parent_of_some ? take(plane * es) : 0;
+    m.vmax = velocity ? take(plane * es) : 0;
     m.tiles_x = (b[k].nx + tx - 1) / tx;
     m.tiles_y = (b[k].ny + ty - 1) / ty;
     m.budget = take((size_t)m.tiles_x * m.tiles_y * 4 * sizeof(double));
@@ -101,8 +103,9 @@ int validate(const rti_block* bl, int nb, const rti_params* p, std::string* why)
   if (!(p->dt > 0) || !(p->g > 0) || !(p->dry_eps >= 0) ||
       (p->precision != RTI_FP32 && p->precision != RTI_FP64) ||
       (p->schedule != RTI_SCHED_PERSISTENT && p->schedule != RTI_SCHED_PER_PASS) ||
-      (p->tile_x != 0 && p->tile_x != kStripW) || p->tile_y < 0 || p->tile_y % 8) {
-    *why = "bad params (dt, g, dry_eps, precision, schedule or tile shape)";
+      (p->tile_x != 0 && p->tile_x != kStripW) || p->tile_y < 0 || p->tile_y % 8 ||
+      (p->track_velocity != 0 && p->track_velocity != 1)) {
+    *why = "bad params (dt, g, dry_eps, precision, schedule, tile shape or track_velocity)";
     return RTI_ERR_INVALID_ARG;
   }
   for (int k = 0; k < nb; ++k) {
@@ -172,7 +175,8 @@ struct Group {
   size_t cap_scen = 0;
   int* d_status = nullptr;
   Bar* d_bar = nullptr;
-  int grid = 0;
+  int grid = 0, grid_track = 0;  // co-resident grids of the two kernel variants
+  bool track = false;            // some member keeps the maximum velocity
   long long spin_cycles = kSpinCycles;
   // pinned staging for table uploads
   char* h_stage = nullptr;
@@ -244,6 +248,7 @@ Blk<T> make_blk(rti_handle* h, int k, int base_index, int scen, int child_first,
   b.emax = (T*)(A + m.emax);
   b.arr = (int*)(A + m.arr);
   b.ring = m.ring ? (T*)(A + m.ring) : nullptr;
+  b.vmax = m.vmax ? (T*)(A + m.vmax) : nullptr;
   b.nx = d.nx;
   b.ny = d.ny;
   b.pitch = m.pitch;
@@ -322,8 +327,11 @@ int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, std::st
     if (c > 0) g->spin_cycles = c;
   }
   if (e == cudaSuccess) {
-    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid, tx, ty)
-                         : persistent_grid<double>(&g->grid, tx, ty);
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid, tx, ty, false)
+                         : persistent_grid<double>(&g->grid, tx, ty, false);
+  if (e == cudaSuccess)
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_track, tx, ty, true)
+                         : persistent_grid<double>(&g->grid_track, tx, ty, true);
   }
   if (e != cudaSuccess) return cuda_err(err, e, "group setup");
   return RTI_OK;
@@ -340,6 +348,7 @@ KParams<T> kparams(Group* g, int nsteps) {
   kp.status = g->d_status;
   kp.bar = g->d_bar;
   kp.nsteps = nsteps;
+  kp.track = g->track ? 1 : 0;
   kp.tx = g->tx;
   kp.ty = g->ty;
   kp.spin_cycles = g->spin_cycles;
@@ -372,8 +381,10 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   std::vector<int> kids;
   std::vector<Tile> tiles;
   long long cells = 0;
+  bool track = false;
   for (size_t mi = 0; mi < g->members.size(); ++mi) {
     rti_handle* h = g->members[mi];
+    track = track || h->params.track_velocity != 0;
     const int base = (int)blks.size();
     const int nb = (int)h->blocks.size();
     std::vector<std::vector<int>> ch(nb);
@@ -428,7 +439,8 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   if (e == cudaSuccess)
     e = grow(&g->d_scen, &g->cap_scen, g->members.size() * sizeof(ScenDev) + 64, &moved);
   if (e != cudaSuccess) return cuda_err(err, e, "device tables");
-  if (moved && g->gexec) {  // the captured graph holds the old pointers
+  // the captured graph holds the old pointers, or the other kernel variant
+  if ((moved || track != g->track) && g->gexec) {
     cudaGraphExecDestroy(g->gexec);
     g->gexec = nullptr;
     g->graph_tried = false;
@@ -475,6 +487,7 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   g->nblk = (int)blks.size();
   g->nkids = (int)kids.size();
   g->cells = cells;
+  g->track = track;
   g->dirty = false;
   return RTI_OK;
 }
@@ -486,9 +499,11 @@ int group_upload_any(Group* g, cudaStream_t st, std::string* err) {
 int launch_any(Group* g, int nsteps, cudaStream_t st, std::string* err) {
   cudaError_t e;
   if (g->prec == RTI_FP32)
-    e = launch_chunk<float>(kparams<float>(g, nsteps), g->sched, g->grid, g->d_counts + 1, st);
+    e = launch_chunk<float>(kparams<float>(g, nsteps), g->sched,
+                            g->track ? g->grid_track : g->grid, g->d_counts + 1, st);
   else
-    e = launch_chunk<double>(kparams<double>(g, nsteps), g->sched, g->grid, g->d_counts + 1, st);
+    e = launch_chunk<double>(kparams<double>(g, nsteps), g->sched,
+                             g->track ? g->grid_track : g->grid, g->d_counts + 1, st);
   if (e != cudaSuccess) return cuda_err(err, e, "chunk launch");
   return RTI_OK;
 }
@@ -571,6 +586,30 @@ __global__ void k_dense_from_plane(const T* plane, int nx, int ny, int pitch, do
        i += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(i / nx), c = (int)(i - (long long)r * nx);
     out[i] = (double)plane[(size_t)(r + kYOff) * pitch + (c + kXOff)];
+  }
+}
+
+// squared cell-centre speed of a state (R11), -1 on a dry cell
+template <class T>
+__device__ __forceinline__ T cell_speed2(T Mw, T Me, T Ns, T Nn, T D, T eps) {
+  if (!(D > eps)) return T(-1);
+  const T u = T(0.5) * (Mw + Me), v = T(0.5) * (Ns + Nn);
+  return (u * u + v * v) / (D * D);
+}
+
+// maximum water velocity of a block: the running maximum, with the current state added
+template <class T>
+__global__ void k_max_velocity(const T* vmax, const T* eta, const T* M, const T* N, const T* hpl,
+                               int nx, int ny, int pitch, T eps, double* out) {
+  const long long n = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / nx), c = (int)(i - (long long)r * nx);
+    const size_t o = (size_t)(r + kYOff) * pitch + (c + kXOff);
+    T m = vmax[o];
+    const T s2 = cell_speed2(M[o], M[o + 1], N[o], N[o + pitch], hpl[o] + eta[o], eps);
+    if (s2 > m) m = s2;
+    out[i] = sqrt((double)m);
   }
 }
 
@@ -738,6 +777,7 @@ int init_block_t(rti_handle* h, int k, const double* dz) {
   for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = cudaMemset(h->arena + m.N[s], 0, plane * es);
   if (e == cudaSuccess)
     e = cudaMemset(h->arena + m.budget, 0, (size_t)m.tiles_x * m.tiles_y * 4 * sizeof(double));
+  if (e == cudaSuccess && m.vmax) e = cudaMemset(h->arena + m.vmax, 0, plane * es);
   if (e != cudaSuccess) return cuda_err(&h->err, e, "initial state");
   return RTI_OK;
 }
@@ -771,7 +811,8 @@ int rti_footprint(const rti_block* blocks, int nblocks, const rti_params* params
   if (rc) return rc;
   const int tx = params->tile_x ? params->tile_x : kDefaultTx;
   const int ty = params->tile_y ? params->tile_y : kDefaultTy;
-  *bytes = plan_layout(blocks, nblocks, params->precision, tx, ty, nullptr, nullptr);
+  *bytes = plan_layout(blocks, nblocks, params->precision, tx, ty, nullptr, nullptr, nullptr,
+                       params->track_velocity != 0);
   return RTI_OK;
 }
 
@@ -804,7 +845,8 @@ int rti_create(const rti_block* blocks, int nblocks, const double* const* bathy,
   h->params.tile_y = params->tile_y ? params->tile_y : kDefaultTy;
   h->blocks.assign(blocks, blocks + nblocks);
   h->arena_bytes = plan_layout(blocks, nblocks, h->prec, h->params.tile_x, h->params.tile_y,
-                               &h->mem, &h->off_status, &h->off_io);
+                               &h->mem, &h->off_status, &h->off_io,
+                               h->params.track_velocity != 0);
   for (int k = 0; k < nblocks; ++k) h->cells += (long long)blocks[k].nx * blocks[k].ny;
   cudaError_t e = cudaSuccess;
   if (device_mem) {
@@ -1014,6 +1056,43 @@ static int get_out(rti_handle* h, int block, double* out, int kind) {
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpy(out, io, n * sizeof(double), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_err(&h->err, e, "outputs");
+  h->d2h += (long long)(n * sizeof(double));
+  return RTI_OK;
+}
+
+int rti_get_max_velocity(rti_handle* h, int block, double* out) {
+  if (bad_block(h, block) || !out) return RTI_ERR_INVALID_ARG;
+  const BlkMem& m = h->mem[block];
+  if (!m.vmax)
+    return set_err(&h->err, RTI_ERR_STATE, "the handle was created without track_velocity");
+  int rc = sync_for_read(h);
+  if (rc) return rc;
+  const rti_block& d = h->blocks[block];
+  const int p = (int)(h->base & 1);
+  cudaError_t e = cudaSuccess;
+  if (d.parent >= 0) {  // the current state's edge fluxes are defined by the parent
+    Group* g = h->self;
+    e = g->prec == RTI_FP32 ? launch_fill_edges<float>(kparams<float>(g, 0), g->grid, p, 0)
+                            : launch_fill_edges<double>(kparams<double>(g, 0), g->grid, p, 0);
+  }
+  double* io = io_plane(h);
+  char* A = h->arena;
+  if (e == cudaSuccess) {
+    if (h->prec == RTI_FP32)
+      k_max_velocity<float><<<kIoBlocks, kIoThreads>>>(
+          (const float*)(A + m.vmax), (const float*)(A + m.eta[p]), (const float*)(A + m.M[p]),
+          (const float*)(A + m.N[p]), (const float*)(A + m.h), d.nx, d.ny, m.pitch,
+          (float)h->params.dry_eps, io);
+    else
+      k_max_velocity<double><<<kIoBlocks, kIoThreads>>>(
+          (const double*)(A + m.vmax), (const double*)(A + m.eta[p]), (const double*)(A + m.M[p]),
+          (const double*)(A + m.N[p]), (const double*)(A + m.h), d.nx, d.ny, m.pitch,
+          h->params.dry_eps, io);
+    e = cudaGetLastError();
+  }
+  const size_t n = (size_t)d.nx * d.ny;
+  if (e == cudaSuccess) e = cudaMemcpy(out, io, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "max velocity");
   h->d2h += (long long)(n * sizeof(double));
   return RTI_OK;
 }
@@ -1277,7 +1356,7 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
   k_noalloc_setup<T><<<1, 256, 0, stream>>>(s, b, tx, ty, tiles_x, tiles_y, steps_done, nsteps);
   cudaError_t e = cudaGetLastError();
   int grid = 0;
-  if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty);
+  if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty, false);
   if (e == cudaSuccess) {
     KParams<T> kp;
     std::memset(&kp, 0, sizeof(kp));
@@ -1323,6 +1402,10 @@ extern "C" int rti_step_noalloc(const rti_block* grid, const rti_params* params,
   if (rc) {
     t_create_err = "rti_step_noalloc: " + why;
     return rc;
+  }
+  if (params->track_velocity) {
+    t_create_err = "rti_step_noalloc: track_velocity needs a plane the state does not have";
+    return RTI_ERR_INVALID_ARG;
   }
   const int tx = params->tile_x ? params->tile_x : kDefaultTx;
   const int ty = params->tile_y ? params->tile_y : kDefaultTy;

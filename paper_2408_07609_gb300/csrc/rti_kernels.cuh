@@ -270,6 +270,10 @@ struct Ar<double> {
     double F = K.cfric * nf * nf * sqrt(m * m + across * across) / (Df * Df * cbrt(Df));
     return ((1.0 - F) * m - adv - P) / (1.0 + F);
   }
+  // squared cell-centre speed (u^2 + v^2) / D^2 (R11)
+  static __device__ __forceinline__ double speed2(double u, double v, double D) {
+    return (u * u + v * v) / (D * D);
+  }
   // Outflow limit: |flux| <= D dx / (4 dt) with D the depth of the cell it drains.
   static __device__ __forceinline__ double limit(double m, double Dlo, double Dhi,
                                                  const MomK<double>& K) {
@@ -295,6 +299,9 @@ struct Ar<float> {
     const float F =
         (K.cfric * nf * nf) * ex2_approx(0.5f * lg2_approx(s2) - 2.33333333f * lg2_approx(Df));
     return __fdividef((1.0f - F) * m - adv - P, 1.0f + F);
+  }
+  static __device__ __forceinline__ float speed2(float u, float v, float D) {
+    return __fdividef(u * u + v * v, D * D);
   }
   static __device__ __forceinline__ float limit(float m, float Dlo, float Dhi,
                                                 const MomK<float>& K) {
@@ -348,6 +355,7 @@ template <class T>
 struct Raw {
   T e, h, m, nn, em;
   float nm;
+  T vm;  // squared-speed maximum (velocity tracking only)
 };
 
 // The march's input rows are staged ahead in shared memory: a ring of kRingD slots per
@@ -372,6 +380,7 @@ template <class T>
 struct __align__(16) RingSlot {
   T e[kRingW], h[kRingW], m[kRingW], nn[kRingW], em[kRingW];
   float nm[kRingW];
+  T vm[kRingW];  // squared-speed maximum, staged only when the block tracks it
 };
 
 // One 16-byte copy, issued only where `issue` holds (a predicate on the instruction, not
@@ -435,11 +444,11 @@ __device__ __forceinline__ void cp_async16x5(bool issue, unsigned d, const void*
       : "memory");
 }
 
-template <class T>
+template <class T, bool kTrack>
 __device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T* h, const T* M,
                                           const T* N, const T* emax, const float* man,
-                                          int rowbase, int pitch, const StageLane& L,
-                                          bool row_ok) {
+                                          const T* vmax, int rowbase, int pitch,
+                                          const StageLane& L, bool row_ok) {
   static_assert(offsetof(RingSlot<T>, h) == kRingW * sizeof(T) &&
                     offsetof(RingSlot<T>, em) == 4 * kRingW * sizeof(T),
                 "state rows kRingW elements apart");
@@ -448,9 +457,10 @@ __device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T*
                                         (unsigned)__cvta_generic_to_shared(&S.e[L.ke]), eta + g,
                                         h + g, M + g, N + g + pitch, emax + g, L.oe);
   cp_async16(row_ok && L.im, &S.nm[L.km], man + (L.om ? rowbase + L.km : rowbase), L.om);
+  if (kTrack) cp_async16(row_ok && L.ie, &S.vm[L.ke], vmax + g, L.oe);
 }
 
-template <class T>
+template <class T, bool kTrack>
 __device__ __forceinline__ Raw<T> read_row(const RingSlot<T>& S, int lane) {
   Raw<T> R;
   R.e = S.e[lane + 2];
@@ -459,6 +469,7 @@ __device__ __forceinline__ Raw<T> read_row(const RingSlot<T>& S, int lane) {
   R.nn = S.nn[lane + 2];
   R.em = S.em[lane + 2];
   R.nm = S.nm[lane + 2];
+  R.vm = kTrack ? S.vm[lane + 2] : T(0);
   return R;
 }
 
@@ -643,7 +654,7 @@ __device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<
 // Step strip td at chunk step s (one warp; ws holds the strip's staged descriptor, the
 // prepass has run). The budget slot of the strip receives sum(eta^{n+1}) and adds the
 // clip, outflow and ring terms.
-template <class T>
+template <class T, bool kTrack>
 __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& ws, Tile td,
                                             int s) {
   constexpr int kRingD = RingD<T>::D;
@@ -668,6 +679,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   T* Nq = b.N[q];
   T* emax = b.emax;
   const bool ring_strip = (td.flags & kTfRing) != 0;
+  T* vmax = b.vmax;  // tracked iff kTrack
   const unsigned full = 0xffffffffu;
 
   const int c = td.x0 - 2 + lane;                            // this lane's column (>= -2)
@@ -691,8 +703,8 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   int rowbase = (y0 - 2 + kYOff) * pitch + x0;
   const StageLane SL = stage_lane<T>(lane, x0, pitch);
   for (int k = 0; k < kRingD - 2; ++k) {
-    stage_row(ws.ring[k], etaP, hh, Mp, Np, emax, man, rowbase + k * pitch, pitch, SL,
-              y0 - 2 + k <= ye);
+    stage_row<T, kTrack>(ws.ring[k], etaP, hh, Mp, Np, emax, man, vmax, rowbase + k * pitch,
+                         pitch, SL, y0 - 2 + k <= ye);
     cp_async_commit();
   }
   Row<T> A = {}, B = {}, C = {};
@@ -710,8 +722,15 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     Nw.nm = cur.nm;
     Nw.mE = __shfl_down_sync(full, m, 1);
     const T nnL = __shfl_up_sync(full, nn, 1);
-    T e = cur.e - (dtdx * (Nw.mE - m) + dtdx * (nn - nS));
     const bool own = own_col && r >= y0 && r < ye;
+    if (kTrack) {  // R11: the state this step starts from (eta^n, M^n, N^n)
+      const T D = cur.h + cur.e;
+      if (own && D > eps) {
+        const T s2 = Ar<T>::speed2(T(0.5) * (m + Nw.mE), T(0.5) * (nS + nn), D);
+        if (s2 > cur.vm) vmax[o] = s2;
+      }
+    }
+    T e = cur.e - (dtdx * (Nw.mE - m) + dtdx * (nn - nS));
     const bool clipped = Nw.H + e < T(0);
     clip_t += (clipped && own) ? -Nw.H - e : T(0);
     e = clipped ? -Nw.H : e;
@@ -826,12 +845,13 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   int slot = 0;  // ring slot of row r
   for (int r = y0 - 2; r <= ye; ++r) {
     // refill the slot of row r - 2: every lane read it before the __syncwarp of row r - 1
-    stage_row(ws.ring[(slot - 2) & (kRingD - 1)], etaP, hh, Mp, Np, emax, man,
-              rowbase + (kRingD - 2) * pitch, pitch, SL, r + kRingD - 2 <= ye);
+    stage_row<T, kTrack>(ws.ring[(slot - 2) & (kRingD - 1)], etaP, hh, Mp, Np, emax, man,
+                         vmax, rowbase + (kRingD - 2) * pitch, pitch, SL,
+                         r + kRingD - 2 <= ye);
     cp_async_commit();
     cp_async_wait<kRingD - 2>();  // row r has landed
     __syncwarp();                 // ... for every lane's chunks
-    const Raw<T> cur = read_row(ws.ring[slot], lane);
+    const Raw<T> cur = read_row<T, kTrack>(ws.ring[slot], lane);
     slot = (slot + 1) & (kRingD - 1);
     rowbase += pitch;
     Row<T> X;
@@ -899,7 +919,8 @@ __device__ __forceinline__ bool grid_barrier(Bar* bar, unsigned& gen, int* statu
 }
 
 // ------------------------------------------------------------------ kernels
-// Steps [s_first, s_first + s_count) of a chunk over every strip of the work list. The
+// Steps [s_first, s_first + s_count) of a chunk over every strip of the work list (the
+// kAnyTrack variant also carries the maximum-velocity update, for groups that need it). The
 // warps take strips from a device counter per step (heavy strips come first in the
 // list), so a slow strip delays no fixed set of others. Counter s & 1 serves step s;
 // the other one is cleared during step s, when no warp can still be taking from it
@@ -917,7 +938,7 @@ struct StepOcc<float> {
   static constexpr int kMinBlocks = 5;
 };
 
-template <class T>
+template <class T, bool kAnyTrack>
 __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
     k_step(KParams<T> kp, int s_first, int s_count) {
   __shared__ WarpSlot<T> slots[kWarps];
@@ -941,7 +962,8 @@ __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
       if ((long long)s >= ws.sc.remaining) continue;  // the scenario has finished
       if ((td.flags & kTfRing) || ws.b.is_child)
         strip_prepass(kp, ws, td, (int)((ws.sc.base + s) & 1));
-      march_strip(kp, ws, td, s);
+      if (kAnyTrack && ws.b.vmax) march_strip<T, kAnyTrack>(kp, ws, td, s);  // velocity tracked
+      else march_strip<T, false>(kp, ws, td, s);
     }
     if (s + 1 < s_first + s_count &&
         !grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go))

@@ -41,6 +41,7 @@ struct Blk {
   int* arr;   // arrival step, -1 if never
   T* ring;    // a parent's fine-to-coarse eta^{n+1} on ring cells, all-ones bits elsewhere
               // (written each step by the strips that read it); null without children
+  T* vmax;    // running max of the squared cell-centre speed; null when not tracked
   int nx, ny, pitch, parent; // parent: index in the batch block table, -1 for a root
   int i0, j0;                // child origin in parent cells
   int child_first, child_count; // children: kids[child_first .. +child_count)
@@ -86,6 +87,7 @@ struct KParams {
   int* status;         // group status (barrier timeout)
   Bar* bar;
   int nsteps;
+  int track;           // some block keeps the maximum velocity (selects the kernel variant)
   int tx, ty;          // tile shape in cells
   long long spin_cycles;
 #ifdef RTI_CHECKED

@@ -36,7 +36,7 @@ class Block(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("g", C.c_double), ("dry_eps", C.c_double),
                 ("arrival_thr", C.c_double), ("precision", C.c_int), ("schedule", C.c_int),
-                ("tile_x", C.c_int), ("tile_y", C.c_int)]
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("track_velocity", C.c_int)]
 
 
 class NoAllocState(C.Structure):
@@ -72,6 +72,7 @@ def lib():
             "rti_get_max_depth": (C.c_int, [_vp, C.c_int, _dp]),
             "rti_get_max_height": (C.c_int, [_vp, C.c_int, _dp]),
             "rti_get_arrival_time": (C.c_int, [_vp, C.c_int, _dp]),
+            "rti_get_max_velocity": (C.c_int, [_vp, C.c_int, _dp]),
             "rti_get_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
             "rti_set_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
             "rti_get_budget": (C.c_int, [_vp, C.c_int, _dp]),
@@ -122,9 +123,9 @@ def _blocks_array(blocks):
 
 
 def make_params(dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01, precision=FP64,
-                schedule=SCHED_PERSISTENT, tile=(0, 0)):
+                schedule=SCHED_PERSISTENT, tile=(0, 0), track_velocity=False):
     return Params(float(dt), float(g), float(dry_eps), float(arrival_thr), int(precision),
-                  int(schedule), int(tile[0]), int(tile[1]))
+                  int(schedule), int(tile[0]), int(tile[1]), int(bool(track_velocity)))
 
 
 def footprint(blocks, params: Params) -> int:
@@ -140,10 +141,12 @@ class Handle:
     """One nested-grid hierarchy resident on the GPU (rti_create)."""
 
     def __init__(self, blocks, bathy, manning, dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01,
-                 precision=FP64, schedule=SCHED_PERSISTENT, tile=(0, 0), device_mem=None):
+                 precision=FP64, schedule=SCHED_PERSISTENT, tile=(0, 0), device_mem=None,
+                 track_velocity=False):
         L = lib()
         self.blocks = [dict(b) for b in blocks]
-        self.params = make_params(dt, g, dry_eps, arrival_thr, precision, schedule, tile)
+        self.params = make_params(dt, g, dry_eps, arrival_thr, precision, schedule, tile,
+                                  track_velocity)
         self.dt = float(dt)
         nb = len(blocks)
         arr = _blocks_array(blocks)
@@ -163,9 +166,9 @@ class Handle:
 
     @classmethod
     def from_scenario(cls, sc, precision=FP64, schedule=SCHED_PERSISTENT, tile=(0, 0),
-                      device_mem=None):
+                      device_mem=None, track_velocity=False):
         h = cls(sc.blocks, sc.bathy, sc.manning, sc.dt, sc.g, sc.dry_eps, sc.arrival_thr,
-                precision, schedule, tile, device_mem)
+                precision, schedule, tile, device_mem, track_velocity)
         for k, dz in enumerate(sc.uplift):
             if dz is not None:
                 h.set_initial_uplift(k, dz)
@@ -219,6 +222,9 @@ class Handle:
 
     def arrival_time(self, k):
         return self._field("rti_get_arrival_time", k)
+
+    def max_velocity(self, k):
+        return self._field("rti_get_max_velocity", k)
 
     def budget(self, k):
         out = np.empty(4)

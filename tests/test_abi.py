@@ -77,3 +77,17 @@ def test_planes_beyond_32_bit_offsets_are_rejected(rti):
     assert e.value.code == -1
     ok = blk(nx=(1 << 20) - 9, ny=2040)  # pitch 2^20, 2045 rows: 2^31 - 3 x 2^20 elements
     assert rti.footprint([ok], rti.make_params(dt=0.5, precision=rti.FP32)) > 0
+
+
+def test_velocity_tracking_adds_a_plane_and_is_refused_without_state(rti):
+    """track_velocity adds one state-precision plane per block to the footprint; the
+    allocation-free entry has no plane for it and refuses it before any device work."""
+    base = rti.footprint([blk(nx=300, ny=200)], rti.make_params(dt=0.5, precision=rti.FP32))
+    more = rti.footprint([blk(nx=300, ny=200)],
+                         rti.make_params(dt=0.5, precision=rti.FP32, track_velocity=True))
+    pitch = (300 + 9 + 31) // 32 * 32
+    assert more - base >= pitch * 205 * 4
+    st = rti.NoAllocState()
+    with pytest.raises(rti.RtiError) as e:
+        rti.step_noalloc(blk(nx=64, ny=64), rti.make_params(1.0, track_velocity=True), st, 0, 1)
+    assert e.value.code == -1 and "track_velocity" in str(e.value)

@@ -8,6 +8,7 @@ oracle; it is held to forecast-level bounds instead of parity:
   wet/dry mismatch (final state)              <= 0.5 % of cells
   cells that arrived in one run but not the other <= 0.1 % of cells that arrived
   arrival-time error (cells arrived in both)  mean <= 1 step, max <= 10 steps
+  max water velocity error                    <= 2 % of the largest speed + 1 cm/s
 
 on C1 (single grid, 1800 steps), the C2 nest (1200 steps) and the three smallest grids
 of the C3 batch (2000 steps).
@@ -19,12 +20,13 @@ from paper_2408_07609_gb300 import scenarios as S
 
 
 def _compare(rti, oracle_mod, sc, steps):
-    h = rti.Handle.from_scenario(sc, precision=rti.FP32)
+    h = rti.Handle.from_scenario(sc, precision=rti.FP32, track_velocity=True)
     h.step(steps)
     h.sync()
     o = oracle_mod.from_scenario(sc)
     o.step(steps)
-    m = dict(eta=0.0, maxh=0.0, wet_mis=0, cells=0, arr_mis=0, arrived=0, arr_err=[])
+    m = dict(eta=0.0, maxh=0.0, wet_mis=0, cells=0, arr_mis=0, arrived=0, arr_err=[],
+             vel=0.0, vmax=0.0)
     for k, b in enumerate(sc.blocks):
         hb = np.asarray(sc.bathy[k])
         e32, e64 = h.get_state(k)[0], o.get_state(k)[0]
@@ -40,6 +42,9 @@ def _compare(rti, oracle_mod, sc, steps):
         m["arr_err"].append(np.abs(ga[ab] - ra[ab]))
         m["arr_mis"] += int(((ga >= 0) != (ra >= 0)).sum())
         m["arrived"] += int((ra >= 0).sum())
+        gv, rv = h.max_velocity(k), o.max_velocity(k)
+        m["vel"] = max(m["vel"], float(np.abs(gv - rv).max()))
+        m["vmax"] = max(m["vmax"], float(rv.max()))
     h.close()
     o.close()
     m["arr_err"] = np.concatenate(m["arr_err"])
@@ -53,6 +58,7 @@ def _check(m, dt):
     assert m["arr_mis"] <= 0.001 * max(m["arrived"], 1), m["arr_mis"]
     if m["arr_err"].size:
         assert m["arr_err"].mean() <= dt and m["arr_err"].max() <= 10 * dt
+    assert m["vel"] <= 0.02 * m["vmax"] + 0.01, (m["vel"], m["vmax"])
 
 
 @pytest.mark.gpu

@@ -273,3 +273,26 @@ def test_smallest_children_fp64(rti, oracle_mod):
     h, o = run_pair(rti, oracle_mod, sc, sc.steps)
     compare_fp64(h, o, len(blocks))
     assert max(abs(o.budget(k)["ring"]) for k in range(2)) > 0
+
+
+def test_max_velocity_fp64_single_grid_and_nest(rti, oracle_mod):
+    """R11: the running maximum of the cell-centre speed, on a single grid with a coast
+    and on the three-level nest (child edges pulled from the parent), against the
+    oracle; a handle created without tracking refuses the read."""
+    for sc in (S.config1(steps=300), S.config2(steps=200)):
+        h = rti.Handle.from_scenario(sc, precision=rti.FP64, track_velocity=True)
+        o = oracle_mod.from_scenario(sc)
+        h.step(sc.steps)
+        h.sync()
+        o.step(sc.steps)
+        for k in range(len(sc.blocks)):
+            g, r = h.max_velocity(k), o.max_velocity(k)
+            assert relerr(g, r) <= TOL64, (sc.name, k, relerr(g, r))
+            assert r.max() > 0 or k > 0
+        compare_fp64(h, o, len(sc.blocks))
+        h.close()
+        o.close()
+    h = rti.Handle.from_scenario(S.config1(nx=40, ny=40, steps=0), precision=rti.FP64)
+    with pytest.raises(rti.RtiError) as e:
+        h.max_velocity(0)
+    assert e.value.code == -8
