@@ -48,6 +48,17 @@ extern "C" {
 #define RTI_FP32 1 /* state and arithmetic in binary32; eta is the deviation from still water;
                       the volume budget and the nesting sums accumulate in binary64 */
 
+/* Fine-to-coarse feedback (Sec. IV-C-2, "JNZSND"): which parent cells take the mean of
+ * their 3x3 child cells (the mean of the wet ones, floored at the parent's ground). */
+#define RTI_NEST_RING 0 /* the boundary cells: the inner ring of the child's footprint */
+#define RTI_NEST_FULL 1 /* every parent cell the child covers (full two-way nesting); all
+                           levels exchange at once, so a cell above a grandchild gets the
+                           child's own level, and the grandchild's mean one step later */
+/* Coarse-to-fine boundary flux ("JNQ"): how a child edge face takes the parent flux. */
+#define RTI_FLUX_LINEAR 0   /* linear along the edge: 2/3, 1/3 weights at the outer fine faces */
+#define RTI_FLUX_CONSTANT 1 /* each fine face takes its coarse face's flux (the edge carries
+                               exactly the coarse discharge) */
+
 #define RTI_SCHED_PERSISTENT 0 /* one cooperative launch per chunk of steps, device-wide barriers */
 #define RTI_SCHED_PER_PASS 1   /* one ordinary launch per step (no device-wide barrier) */
 
@@ -74,6 +85,8 @@ typedef struct {
   int tile_y;         /* strip height in cells, a multiple of 8; 0 = 64 */
   int track_velocity; /* 1: keep the maximum water velocity (one more plane per block and a
                          read of it per cell-step); 0: off. Not for rti_step_noalloc. */
+  int nest_feedback;  /* RTI_NEST_RING (0, the default) or RTI_NEST_FULL */
+  int nest_flux;      /* RTI_FLUX_LINEAR (0, the default) or RTI_FLUX_CONSTANT */
 } rti_params;
 
 typedef struct rti_handle rti_handle;

@@ -41,9 +41,13 @@ class _Block(C.Structure):
                 ("i0", C.c_int), ("j0", C.c_int), ("dx", C.c_double), ("bc", C.c_int * 4)]
 
 
+NEST_RING, NEST_FULL = 0, 1
+FLUX_LINEAR, FLUX_CONSTANT = 0, 1
+
+
 class _Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("g", C.c_double), ("dry_eps", C.c_double),
-                ("arrival_thr", C.c_double)]
+                ("arrival_thr", C.c_double), ("nest_feedback", C.c_int), ("nest_flux", C.c_int)]
 
 
 _libs = {}
@@ -94,7 +98,7 @@ class Oracle:
     """
 
     def __init__(self, blocks, bathy, manning, dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01,
-                 lib_path=None):
+                 lib_path=None, nest_feedback=NEST_RING, nest_flux=FLUX_LINEAR):
         self._L = L = lib(lib_path)
         nb = len(blocks)
         arr = (_Block * nb)()
@@ -111,7 +115,7 @@ class Oracle:
         hp = (C.POINTER(C.c_double) * nb)(*[_dptr(x) for x in self._h])
         npp = (C.POINTER(C.c_float) * nb)(
             *[x.ctypes.data_as(C.POINTER(C.c_float)) for x in self._n])
-        prm = _Params(dt, g, dry_eps, arrival_thr)
+        prm = _Params(dt, g, dry_eps, arrival_thr, int(nest_feedback), int(nest_flux))
         err = C.c_int(0)
         self.blocks = [dict(b) for b in blocks]
         self.dt = dt

@@ -36,12 +36,22 @@
  *   R7  coarse->fine: each child edge face takes the parent flux on the coarse face it
  *       lies on, linearly interpolated along the edge (weights 2/3, 1/3 at the outer fine
  *       faces, neighbour clamped at the segment ends); no time interpolation.
+ *       Option ORC_FLUX_CONSTANT: the three fine faces of a coarse face all take its
+ *       flux unchanged (piecewise constant, so the edge carries exactly the coarse
+ *       face's discharge).
  *   R8  fine->coarse: parent cells on the inner ring of the child footprint take the
  *       Listing 5 mean of their 3x3 child cells (x outer, y inner, FP64 sum, times 1/9).
  *       Only wet child cells enter the mean (sum times 1/count; all nine wet gives the
  *       listing's formula exactly); the result is floored at the parent's ground level
  *       -h; a patch with no wet cell leaves the parent's own value. Averaging dry land
  *       levels into a sea cell would break the lake at rest.
+ *       Option ORC_NEST_FULL: every parent cell the child covers takes that mean (full
+ *       two-way nesting). The exchange is simultaneous, as a pack-then-unpack of every
+ *       level's messages: all means are formed from the levels the mass step left,
+ *       before any block receives. A parent cell above a grandchild therefore gets the
+ *       child's own level there; the grandchild's mean reaches it one step later. With
+ *       the ring option the order does not matter: the 3-cell nesting margin keeps a
+ *       ring's patches away from the cells the child itself receives.
  *   R9  after R8: on wet cells, etamax = max(etamax, eta); the arrival step is recorded
  *       when etamax first reaches the threshold (>=).
  *   R10 initial state: eta0 = max(dz, -h) on sea cells, -h on land, fluxes zero.
@@ -138,7 +148,9 @@ static int check_blocks(const orc_block* bl, int nb, const double* const* bathy,
 orc_state* orc_create(const orc_block* blocks, int nblocks, const double* const* bathy,
                       const float* const* manning, const orc_params* p, int* err) {
   int e = ORC_OK;
-  if (!blocks || nblocks <= 0 || !bathy || !manning || !p || !(p->dt > 0) || !(p->g > 0))
+  if (!blocks || nblocks <= 0 || !bathy || !manning || !p || !(p->dt > 0) || !(p->g > 0) ||
+      (p->nest_feedback != ORC_NEST_RING && p->nest_feedback != ORC_NEST_FULL) ||
+      (p->nest_flux != ORC_FLUX_LINEAR && p->nest_flux != ORC_FLUX_CONSTANT))
     e = ORC_ERR_INVALID_ARG;
   for (int k = 0; e == ORC_OK && k < nblocks; ++k)
     if (!bathy[k] || !manning[k]) e = ORC_ERR_INVALID_ARG;
@@ -278,15 +290,23 @@ static void mass_block(oblk* b, const orc_params* p) {
   }
 }
 
-/* ---- R8: fine->coarse ring (Listing 5) ---- */
-static void ring_child(orc_state* s, int k) {
-  oblk* c = &s->b[k];
-  oblk* P = &s->b[c->d.parent];
+/* ---- R8: fine->coarse (Listing 5) ---- */
+/* does parent cell (I, J) of a child footprint a x bb cells receive the child's mean? */
+static int receives(const orc_params* p, int I, int J, int a, int bb) {
+  if (p->nest_feedback == ORC_NEST_FULL) return 1;
+  return I == 0 || I == a - 1 || J == 0 || J == bb - 1; /* the inner ring */
+}
+
+/* pack: the mean of the wet child cells of every receiving parent cell of child k, from
+ * the child's eta^{n+1}, into out[J * a + I]; NAN where the patch has no wet cell or
+ * the cell does not receive */
+static void pack_child(const orc_state* s, int k, double* out) {
+  const oblk* c = &s->b[k];
   int a = c->nx / 3, bb = c->ny / 3;
-  double dx2 = P->dx * P->dx;
   for (int J = 0; J < bb; ++J) {
     for (int I = 0; I < a; ++I) {
-      if (!(I == 0 || I == a - 1 || J == 0 || J == bb - 1)) continue;
+      out[(size_t)J * a + I] = NAN;
+      if (!receives(&s->p, I, J, a, bb)) continue;
       double sum = 0.0;
       int wet = 0;
       for (int x = 3 * I; x < 3 * I + 3; ++x) {   /* outer: x (the paper's J) */
@@ -298,14 +318,45 @@ static void ring_child(orc_state* s, int k) {
           }
         }
       }
-      if (wet == 0) continue; /* dry patch: the parent keeps its own value */
+      if (wet == 0) continue;                  /* dry patch: the parent keeps its value */
+      out[(size_t)J * a + I] = sum * (1.0 / (double)wet); /* all 9 wet: SUMZ * (1.0/9.0) */
+    }
+  }
+}
+
+/* unpack: the parent of child k takes the packed means, floored at its ground level */
+static void unpack_child(orc_state* s, int k, const double* in) {
+  const oblk* c = &s->b[k];
+  oblk* P = &s->b[c->d.parent];
+  int a = c->nx / 3, bb = c->ny / 3;
+  double dx2 = P->dx * P->dx;
+  for (int J = 0; J < bb; ++J) {
+    for (int I = 0; I < a; ++I) {
+      double avg = in[(size_t)J * a + I];
+      if (isnan(avg)) continue;
       size_t pc = C(P, c->d.i0 + I, c->d.j0 + J);
-      double avg = sum * (1.0 / (double)wet); /* all 9 wet: SUMZ * (1.0/9.0) */
       if (avg < -P->h[pc]) avg = -P->h[pc];
       P->ring += (avg - P->eta1[pc]) * dx2;
       P->eta1[pc] = avg;
     }
   }
+}
+
+/* every child packs, then every parent unpacks (finest children first) */
+static void fine_to_coarse(orc_state* s) {
+  double** buf = (double**)calloc((size_t)s->nb, sizeof(double*));
+  if (!buf) abort();
+  for (int k = 0; k < s->nb; ++k) {
+    const oblk* c = &s->b[k];
+    if (c->d.parent < 0) continue;
+    buf[k] = (double*)malloc((size_t)(c->nx / 3) * (size_t)(c->ny / 3) * sizeof(double));
+    if (!buf[k]) abort();
+    pack_child(s, k, buf[k]);
+  }
+  for (int k = s->nb - 1; k >= 0; --k)
+    if (buf[k]) unpack_child(s, k, buf[k]);
+  for (int k = 0; k < s->nb; ++k) free(buf[k]);
+  free(buf);
 }
 
 /* ---- R2/R3 helpers. x-faces (f,j) separate cells (f-1,j) and (f,j). ---- */
@@ -493,9 +544,9 @@ static void momentum_block(oblk* b, const orc_params* p) {
 
 /* ---- R7: coarse->fine edge fluxes ---- */
 /* value for fine face number t along an edge whose coarse faces are v(k), k = 0..K-1 */
-static double interp_edge(const double* v, int K, int t) {
+static double interp_edge(const double* v, int K, int t, int constant) {
   int k = t / 3, sub = t % 3;
-  if (sub == 1) return v[k];
+  if (sub == 1 || constant) return v[k];
   int kn = sub == 0 ? k - 1 : k + 1;
   if (kn < 0) kn = 0;
   if (kn > K - 1) kn = K - 1;
@@ -506,19 +557,20 @@ static void edges_child(orc_state* s, int k) {
   oblk* c = &s->b[k];
   const oblk* P = &s->b[c->d.parent];
   int a = c->nx / 3, bb = c->ny / 3, i0 = c->d.i0, j0 = c->d.j0;
+  int cst = s->p.nest_flux == ORC_FLUX_CONSTANT;
   double* v = (double*)malloc((size_t)(a > bb ? a : bb) * sizeof(double));
   if (!v) abort();
   /* west and east: parent x-faces i0 and i0+a, parent rows j0..j0+bb-1 */
   for (int side = 0; side < 2; ++side) {
     int F = side == 0 ? i0 : i0 + a, f = side == 0 ? 0 : c->nx;
     for (int t = 0; t < bb; ++t) v[t] = P->M1[FX(P, F, j0 + t)];
-    for (int j = 0; j < c->ny; ++j) c->M1[FX(c, f, j)] = interp_edge(v, bb, j);
+    for (int j = 0; j < c->ny; ++j) c->M1[FX(c, f, j)] = interp_edge(v, bb, j, cst);
   }
   /* south and north: parent y-faces j0 and j0+bb, parent columns i0..i0+a-1 */
   for (int side = 0; side < 2; ++side) {
     int G = side == 0 ? j0 : j0 + bb, g = side == 0 ? 0 : c->ny;
     for (int t = 0; t < a; ++t) v[t] = P->N1[FY(P, i0 + t, G)];
-    for (int i = 0; i < c->nx; ++i) c->N1[FY(c, i, g)] = interp_edge(v, a, i);
+    for (int i = 0; i < c->nx; ++i) c->N1[FY(c, i, g)] = interp_edge(v, a, i, cst);
   }
   free(v);
 }
@@ -535,8 +587,7 @@ int orc_step(orc_state* s, int nsteps) {
     long step = s->step + 1;
     for (int k = 0; k < s->nb; ++k) track_speed(&s->b[k], &s->p);
     for (int k = 0; k < s->nb; ++k) mass_block(&s->b[k], &s->p);
-    for (int k = s->nb - 1; k >= 0; --k) /* finest first */
-      if (s->b[k].d.parent >= 0) ring_child(s, k);
+    fine_to_coarse(s);
     for (int k = 0; k < s->nb; ++k) {
       oblk* b = &s->b[k];
       for (size_t c = 0; c < (size_t)b->nx * b->ny; ++c) track_cell(b, c, step, &s->p);

@@ -12,7 +12,7 @@
  * Sec. V-A), in the order of the time-integration loop of Sec. IV-A / Fig. 2:
  * mass -> child-to-parent eta -> momentum -> parent-to-child flux -> output
  * update -> buffer swap. The paper gives the PDEs only; every discrete choice
- * made here is a stated reading (R1..R10 in the comments of rti_oracle.c).
+ * made here is a stated reading (R1..R11 in the comments of rti_oracle.c).
  */
 #ifndef RTI_ORACLE_H
 #define RTI_ORACLE_H
@@ -39,11 +39,18 @@ typedef struct {
   int bc[4];   /* west, east, south, north: ORC_BC_WALL or ORC_BC_RADIATION (roots only) */
 } orc_block;
 
+#define ORC_NEST_RING 0     /* fine->coarse: the parent cells on the footprint's inner ring */
+#define ORC_NEST_FULL 1     /* fine->coarse: every parent cell the child covers */
+#define ORC_FLUX_LINEAR 0   /* coarse->fine: flux interpolated linearly along the edge */
+#define ORC_FLUX_CONSTANT 1 /* coarse->fine: each fine face takes its coarse face's flux */
+
 typedef struct {
   double dt;          /* s, same on every level */
   double g;           /* m/s^2 */
   double dry_eps;     /* m: a cell is wet when h + eta > dry_eps */
   double arrival_thr; /* m: arrival when max eta first reaches this */
+  int nest_feedback;  /* ORC_NEST_RING or ORC_NEST_FULL */
+  int nest_flux;      /* ORC_FLUX_LINEAR or ORC_FLUX_CONSTANT */
 } orc_params;
 
 typedef struct orc_state orc_state;
@@ -74,7 +81,7 @@ int orc_get_arrival_time(const orc_state* s, int block, double* out);
 int orc_get_max_velocity(const orc_state* s, int block, double* out);
 /* out[0] = water volume sum (h+eta) dx^2, out[1] = cumulative volume that left through
  * the block boundary, out[2] = cumulative volume added by the dry clip, out[3] = cumulative
- * volume changed by the fine-to-coarse replacement of ring cells. */
+ * volume changed by the fine-to-coarse replacement of parent cells (R8). */
 int orc_get_budget(const orc_state* s, int block, double* out);
 
 #ifdef __cplusplus

@@ -104,8 +104,11 @@ int validate(const rti_block* bl, int nb, const rti_params* p, std::string* why)
       (p->precision != RTI_FP32 && p->precision != RTI_FP64) ||
       (p->schedule != RTI_SCHED_PERSISTENT && p->schedule != RTI_SCHED_PER_PASS) ||
       (p->tile_x != 0 && p->tile_x != kStripW) || p->tile_y < 0 || p->tile_y % 8 ||
-      (p->track_velocity != 0 && p->track_velocity != 1)) {
-    *why = "bad params (dt, g, dry_eps, precision, schedule, tile shape or track_velocity)";
+      (p->track_velocity != 0 && p->track_velocity != 1) ||
+      (p->nest_feedback != RTI_NEST_RING && p->nest_feedback != RTI_NEST_FULL) ||
+      (p->nest_flux != RTI_FLUX_LINEAR && p->nest_flux != RTI_FLUX_CONSTANT)) {
+    *why = "bad params (dt, g, dry_eps, precision, schedule, tile shape, track_velocity "
+           "or nesting options)";
     return RTI_ERR_INVALID_ARG;
   }
   for (int k = 0; k < nb; ++k) {
@@ -261,6 +264,8 @@ Blk<T> make_blk(rti_handle* h, int k, int base_index, int scen, int child_first,
   b.scen = scen;
   b.is_child = d.parent >= 0;
   b.tiles_x = (d.nx + tx - 1) / tx;
+  b.nest = (p.nest_feedback == RTI_NEST_FULL ? kNestFull : 0) |
+           (p.nest_flux == RTI_FLUX_CONSTANT ? kNestConst : 0);
   b.budget = (double*)(A + m.budget);
   b.status = (int*)(A + h->off_status);
   const double dt = p.dt, dx = d.dx;
@@ -410,14 +415,15 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
           if (t.y0 == 0) t.flags |= kTfSouth;
           if (t.y0 + g->ty >= d.ny) t.flags |= kTfNorth;
           // the strip recomputes eta^{n+1} on a 2-cell halo: flag it when that halo
-          // meets the inner ring of a child footprint
+          // meets the inner ring of a child footprint (any of it with full feedback)
           const int hx0 = t.x0 - 2, hy0 = t.y0 - 2, hx1 = t.x0 + g->tx + 2, hy1 = t.y0 + g->ty + 2;
+          const bool full = h->params.nest_feedback == RTI_NEST_FULL;
           for (int c : ch[k]) {
             const rti_block& cd = h->blocks[c];
             int a0 = cd.i0, a1 = cd.i0 + cd.nx / 3, b0 = cd.j0, b1 = cd.j0 + cd.ny / 3;
             bool meets = hx0 < a1 && a0 < hx1 && hy0 < b1 && b0 < hy1;
             bool inner = hx0 >= a0 + 1 && hx1 <= a1 - 1 && hy0 >= b0 + 1 && hy1 <= b1 - 1;
-            if (meets && !inner) t.flags |= kTfRing;
+            if (meets && (full || !inner)) t.flags |= kTfRing;
           }
           tiles.push_back(t);
         }

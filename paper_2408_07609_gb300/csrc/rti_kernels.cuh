@@ -110,13 +110,14 @@ __device__ __forceinline__ double interp3(double vk, double vn) { return (2.0 * 
 __device__ __forceinline__ float interp3(float vk, float vn) { return (2.0f * vk + vn) / 3.0f; }
 
 // Fine face t of an edge whose coarse faces are v(k), k = 0..K-1: the coarse value at
-// the middle fine face, (2 v_k + v_{k+-1}) / 3 at the outer ones, neighbour clamped.
+// the middle fine face, (2 v_k + v_{k+-1}) / 3 at the outer ones, neighbour clamped;
+// with `constant` every fine face takes v_k.
 template <class T>
 __device__ __forceinline__ T edge_interp(const T* arr, const Blk<T>& P, int fixed, int start,
-                                         int K, int t, bool along_y) {
+                                         int K, int t, bool along_y, bool constant) {
   int k = t / 3, sub = t - 3 * k;
   const T vk = along_y ? arr[ix(P, fixed, start + k)] : arr[ix(P, start + k, fixed)];
-  if (sub == 1) return vk;
+  if (sub == 1 || constant) return vk;
   int kn = sub == 0 ? k - 1 : k + 1;
   kn = kn < 0 ? 0 : (kn > K - 1 ? K - 1 : kn);
   const T vn = along_y ? arr[ix(P, fixed, start + kn)] : arr[ix(P, start + kn, fixed)];
@@ -128,7 +129,7 @@ template <class T>
 __device__ __forceinline__ T face_m(const Blk<T>& b, const Blk<T>& P, int p, int f, int j) {
   if (b.is_child && (f == 0 || f == b.nx)) {
     int F = b.i0 + (f == 0 ? 0 : b.nx / 3);
-    return edge_interp<T>(P.M[p], P, F, b.j0, b.ny / 3, j, true);
+    return edge_interp<T>(P.M[p], P, F, b.j0, b.ny / 3, j, true, (b.nest & kNestConst) != 0);
   }
   return b.M[p][ix(b, f, j)];
 }
@@ -136,7 +137,7 @@ template <class T>
 __device__ __forceinline__ T face_n(const Blk<T>& b, const Blk<T>& P, int p, int i, int g) {
   if (b.is_child && (g == 0 || g == b.ny)) {
     int G = b.j0 + (g == 0 ? 0 : b.ny / 3);
-    return edge_interp<T>(P.N[p], P, G, b.i0, b.nx / 3, i, false);
+    return edge_interp<T>(P.N[p], P, G, b.i0, b.nx / 3, i, false, (b.nest & kNestConst) != 0);
   }
   return b.N[p][ix(b, i, g)];
 }
@@ -167,7 +168,8 @@ __device__ T child_eta_next(const Blk<T>& c, const Blk<T>& P, int p, int x, int 
 
 // ------------------------------------------------------------------ fine -> coarse (R8)
 // Patch (u, v) of child c (parent cell (c.i0 + u, c.j0 + v) of block P, on the inner
-// ring of c's footprint): if the 3x3 child patch has a wet cell, `out` gets the mean of
+// ring of c's footprint, or anywhere on it with full feedback): if the 3x3 child patch
+// has a wet cell, `out` gets the mean of
 // the wet child levels at eta^{n+1} (recomputed from the child's level p; binary64
 // accumulator, Listing 5 order: x outer, y inner), floored at -hP.
 template <class T>
@@ -586,8 +588,11 @@ __device__ __forceinline__ void stage_strip(const KParams<T>& kp, WarpSlot<T>& w
 // Prepass of a strip over the region its march reads: columns x0-2..x0+29, rows
 // y0-2..ye of cells and x-faces, y-faces up to row ye+1. A child's edge faces there get
 // the parent's current fluxes (R7), stored into the child's own level-p arrays, whose
-// edge entries nothing else reads; a parent's ring cells there get their fine-to-coarse
-// eta^{n+1} or "none" (R8) in the ring plane. The items of the region are spread over
+// edge entries nothing else reads; a parent's ring cells there (every covered cell with
+// full feedback) get their fine-to-coarse eta^{n+1} or "none" (R8) in the ring plane.
+// The means come from the children's own mass step, so with full feedback a cell above
+// a grandchild takes the child's level, as an exchange of every level at once gives.
+// The items of the region are spread over
 // the lanes; strips that overlap store the same values, and __syncwarp orders the
 // stores before the march's loads. Kept out of line so that the march's registers do
 // not pay for the nesting arithmetic.
@@ -615,20 +620,27 @@ __device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<
     }
   }
   if (td.flags & kTfRing) {
+    const bool full = (b.nest & kNestFull) != 0;
     const int c0 = max(cx0, 0), c1 = min(cx1, nx), r0 = max(ry0, 0), r1 = min(ry1, ny);
     for (int q = 0; q < b.child_count; ++q) {
       const Blk<T> ch = RTI_BLK(kp, RTI_KID(kp, b.child_first + q));
       const int a0 = ch.i0, a1 = ch.i0 + ch.nx / 3, b0 = ch.j0, b1 = ch.j0 + ch.ny / 3;
       // the footprint's inner ring within the region: rows b0 and b1-1 (all columns),
-      // columns a0 and a1-1 (rows strictly between)
+      // columns a0 and a1-1 (rows strictly between); with full feedback, the footprint
+      // within the region, row by row
       const int hc0 = max(c0, a0), hc1 = min(c1, a1), nh = max(hc1 - hc0, 0);
       const int vr0 = max(r0, b0 + 1), vr1 = min(r1, b1 - 1), nv = max(vr1 - vr0, 0);
       const bool rb = b0 >= r0 && b0 < r1, rt = b1 - 1 >= r0 && b1 - 1 < r1 && b1 - 1 != b0;
       const bool cl = a0 >= c0 && a0 < c1, cr = a1 - 1 >= c0 && a1 - 1 < c1 && a1 - 1 != a0;
       const int n0 = rb ? nh : 0, n1 = rt ? nh : 0, n2 = cl ? nv : 0, n3 = cr ? nv : 0;
-      for (int k = lane; k < n0 + n1 + n2 + n3; k += 32) {
+      const int fr0 = max(r0, b0), nf = max(min(r1, b1) - fr0, 0);
+      const int n = full ? nh * nf : n0 + n1 + n2 + n3;
+      for (int k = lane; k < n; k += 32) {
         int I, J;
-        if (k < n0) {
+        if (full) {
+          J = fr0 + k / nh;
+          I = hc0 + (k - (k / nh) * nh);
+        } else if (k < n0) {
           I = hc0 + k;
           J = b0;
         } else if (k < n0 + n1) {

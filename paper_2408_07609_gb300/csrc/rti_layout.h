@@ -49,6 +49,7 @@ struct Blk {
   int scen;   // scenario slot (ScenDev index)
   int is_child;
   int tiles_x;     // tiles along x (tile slot = ty_index * tiles_x + tx_index)
+  int nest;        // kNest* bits of the owning handle's nesting options
   double* budget;  // 4 doubles per tile of this block: sum(eta) snapshot, clip, outflow, ring
   int* status;     // the owning handle's device status word
   // constants in the state precision (all exactly the values the oracle uses in FP64)
@@ -60,6 +61,10 @@ struct Blk {
   const char* hi;
 #endif
 };
+
+// nesting options of a block (Blk::nest)
+constexpr int kNestFull = 1;   // fine-to-coarse feedback on every covered parent cell
+constexpr int kNestConst = 2;  // piecewise-constant coarse-to-fine edge flux
 
 struct ScenDev {
   long long base;    // steps completed before this chunk

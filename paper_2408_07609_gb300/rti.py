@@ -16,6 +16,8 @@ from .build import LIB
 FP64, FP32 = 0, 1
 SCHED_PERSISTENT, SCHED_PER_PASS = 0, 1
 BC_WALL, BC_RADIATION = 0, 1
+NEST_RING, NEST_FULL = 0, 1        # fine-to-coarse feedback: boundary ring, every covered cell
+FLUX_LINEAR, FLUX_CONSTANT = 0, 1  # coarse-to-fine edge flux: linear along the edge, constant
 
 OK = 0
 ERR = {-1: "INVALID_ARG", -2: "CFL", -3: "NESTING", -4: "OOM", -5: "NONFINITE", -6: "TIMEOUT",
@@ -36,7 +38,8 @@ class Block(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("g", C.c_double), ("dry_eps", C.c_double),
                 ("arrival_thr", C.c_double), ("precision", C.c_int), ("schedule", C.c_int),
-                ("tile_x", C.c_int), ("tile_y", C.c_int), ("track_velocity", C.c_int)]
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("track_velocity", C.c_int),
+                ("nest_feedback", C.c_int), ("nest_flux", C.c_int)]
 
 
 class NoAllocState(C.Structure):
@@ -123,9 +126,12 @@ def _blocks_array(blocks):
 
 
 def make_params(dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01, precision=FP64,
-                schedule=SCHED_PERSISTENT, tile=(0, 0), track_velocity=False):
+                schedule=SCHED_PERSISTENT, tile=(0, 0), track_velocity=False,
+                nest_feedback=None, nest_flux=None):
     return Params(float(dt), float(g), float(dry_eps), float(arrival_thr), int(precision),
-                  int(schedule), int(tile[0]), int(tile[1]), int(bool(track_velocity)))
+                  int(schedule), int(tile[0]), int(tile[1]), int(bool(track_velocity)),
+                  NEST_RING if nest_feedback is None else int(nest_feedback),
+                  FLUX_LINEAR if nest_flux is None else int(nest_flux))
 
 
 def footprint(blocks, params: Params) -> int:
@@ -142,11 +148,11 @@ class Handle:
 
     def __init__(self, blocks, bathy, manning, dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01,
                  precision=FP64, schedule=SCHED_PERSISTENT, tile=(0, 0), device_mem=None,
-                 track_velocity=False):
+                 track_velocity=False, nest_feedback=None, nest_flux=None):
         L = lib()
         self.blocks = [dict(b) for b in blocks]
         self.params = make_params(dt, g, dry_eps, arrival_thr, precision, schedule, tile,
-                                  track_velocity)
+                                  track_velocity, nest_feedback, nest_flux)
         self.dt = float(dt)
         nb = len(blocks)
         arr = _blocks_array(blocks)
@@ -166,9 +172,10 @@ class Handle:
 
     @classmethod
     def from_scenario(cls, sc, precision=FP64, schedule=SCHED_PERSISTENT, tile=(0, 0),
-                      device_mem=None, track_velocity=False):
+                      device_mem=None, track_velocity=False, nest_feedback=None,
+                      nest_flux=None):
         h = cls(sc.blocks, sc.bathy, sc.manning, sc.dt, sc.g, sc.dry_eps, sc.arrival_thr,
-                precision, schedule, tile, device_mem, track_velocity)
+                precision, schedule, tile, device_mem, track_velocity, nest_feedback, nest_flux)
         for k, dz in enumerate(sc.uplift):
             if dz is not None:
                 h.set_initial_uplift(k, dz)

@@ -48,6 +48,15 @@ def test_footprint_and_validation_on_host(rti):
     with pytest.raises(rti.RtiError) as e:
         rti.footprint([blk()], rti.make_params(dt=0.5, tile=(48, 16)))
     assert e.value.code == -1
+    # nesting options: both values of each are accepted, nothing else
+    for fb in (rti.NEST_RING, rti.NEST_FULL):
+        for fl in (rti.FLUX_LINEAR, rti.FLUX_CONSTANT):
+            assert rti.footprint([blk()], rti.make_params(dt=0.5, nest_feedback=fb,
+                                                          nest_flux=fl)) == fp
+    for kw in (dict(nest_feedback=2), dict(nest_flux=-1)):
+        with pytest.raises(rti.RtiError) as e:
+            rti.footprint([blk()], rti.make_params(dt=0.5, **kw))
+        assert e.value.code == -1
 
 
 def test_create_rejects_cfl_before_any_device_call(rti):

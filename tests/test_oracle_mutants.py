@@ -4,7 +4,6 @@ test_oracle_pins fails. The product code is never touched."""
 import functools
 import os
 import sys
-import os
 import subprocess
 import types
 
@@ -33,8 +32,17 @@ MUTANTS = [
     ("radiation: inward", "return sign * (sqrt(", "return -sign * (sqrt("),
     ("nesting: fine faces not interpolated", "return (2.0 * v[k] + v[kn]) / 3.0;",
      "return v[kn];"),
-    ("nesting: ring mean without the 1/count", "double avg = sum * (1.0 / (double)wet);",
-     "double avg = sum * (1.0 / 8.0);"),
+    ("nesting: ring mean without the 1/count",
+     "out[(size_t)J * a + I] = sum * (1.0 / (double)wet);",
+     "out[(size_t)J * a + I] = sum * (1.0 / 8.0);"),
+    ("nesting: full feedback still only on the ring",
+     "if (p->nest_feedback == ORC_NEST_FULL) return 1;",
+     "if (p->nest_feedback == -1) return 1;"),
+    ("nesting: constant flux still interpolated", "if (sub == 1 || constant) return v[k];",
+     "if (sub == 1) return v[k];"),
+    ("nesting: full feedback patch one child row off",
+     "for (int y = 3 * J; y < 3 * J + 3; ++y) { /* inner",
+     "for (int y = 3 * J + 1; y < 3 * J + 4 && y < c->ny; ++y) { /* inner"),
     ("outputs: strict arrival threshold", "e >= p->arrival_thr", "e > p->arrival_thr"),
     ("outputs: max tracked on dry cells", "if (b->h[c] + e > p->dry_eps && e > b->emax[c])",
      "if (e > b->emax[c])"),
@@ -57,6 +65,8 @@ BATTERY = [
     pins.test_max_and_arrival_are_functions_of_history,
     pins.test_nest_constant_field_ring_average,
     pins.test_nest_edge_flux_reproduces_linear_profile,
+    pins.test_constant_flux_gives_each_fine_face_its_coarse_face,
+    pins.test_full_feedback_sets_every_covered_cell_to_the_child_mean,
     pins.test_mirror_and_transpose_symmetry_bitwise,
     pins.test_friction_matches_manning_ode,
     pins.test_radiation_west_edge_absorbs,
@@ -85,7 +95,8 @@ def test_pins_catch_planted_mistake(oracle_mod, tmp_path, name, old, new):
         Oracle=functools.partial(oracle_mod.Oracle, lib_path=so),
         OracleError=oracle_mod.OracleError,
         from_scenario=functools.partial(oracle_mod.from_scenario, lib_path=so),
-        SRC=oracle_mod.SRC)
+        SRC=oracle_mod.SRC, NEST_RING=oracle_mod.NEST_RING, NEST_FULL=oracle_mod.NEST_FULL,
+        FLUX_LINEAR=oracle_mod.FLUX_LINEAR, FLUX_CONSTANT=oracle_mod.FLUX_CONSTANT)
     for pin in BATTERY:
         try:
             pin(fake)

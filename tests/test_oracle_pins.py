@@ -82,15 +82,16 @@ def _rest_hierarchy(scen):
     return sc
 
 
-def test_lake_at_rest_nested_bitwise(oracle_mod):
+def test_lake_at_rest_nested_bitwise(oracle_mod, nest_feedback=0, nest_flux=0, steps=10000):
     """eta = 0 on sea, -h on land, no flux, over rough bathymetry with land and three
     nested levels: every term of Eqs. 2-3 vanishes, bitwise, for 10^4 steps."""
     from paper_2408_07609_gb300 import scenarios as S
 
     sc = _rest_hierarchy(S)
     assert any((h <= 0).any() for h in sc.bathy) and any((h > 0).any() for h in sc.bathy)
-    o = oracle_mod.Oracle(sc.blocks, sc.bathy, sc.manning, sc.dt)
-    o.step(10000)
+    o = oracle_mod.Oracle(sc.blocks, sc.bathy, sc.manning, sc.dt, nest_feedback=nest_feedback,
+                          nest_flux=nest_flux)
+    o.step(steps)
     for k in range(len(sc.blocks)):
         e, M, N = o.get_state(k)
         rest = np.where(sc.bathy[k] > 0, 0.0, -sc.bathy[k])
@@ -310,14 +311,15 @@ def test_nest_edge_flux_reproduces_linear_profile(oracle_mod):
         assert not np.allclose(Mc[3:-3, f], np.repeat(Mp[J0 + 1:J0 + 17, 31], 3), rtol=1e-9)
 
 
-def test_nested_budget_closes(oracle_mod):
+def test_nested_budget_closes(oracle_mod, nest_feedback=0, nest_flux=0):
     """With nesting, each block's budget closes: V = V0 - outflow + clip + ring."""
     from paper_2408_07609_gb300 import scenarios as S
 
     sc = S.coastal_hierarchy("b", 5, (60, 54, 810.0), [(1, 36, 36), (1, 27, 27)], dt=0.5,
                              steps=0, shelf_w=8e3, slope_w=10e3, wiggle=1e3, coast_frac=0.6,
                              land_frac=0.4, source=dict(kind="gauss", sigma=4e3, peak=2.0))
-    o = oracle_mod.Oracle(sc.blocks, sc.bathy, sc.manning, sc.dt)
+    o = oracle_mod.Oracle(sc.blocks, sc.bathy, sc.manning, sc.dt, nest_feedback=nest_feedback,
+                          nest_flux=nest_flux)
     for k, dz in enumerate(sc.uplift):
         if dz is not None:
             o.set_initial_uplift(k, dz)
@@ -329,10 +331,10 @@ def test_nested_budget_closes(oracle_mod):
     assert o.budget(1)["outflow"] != 0 and o.budget(0)["ring"] != 0
 
 
-def test_nested_plane_wave_matches_fine_grid(oracle_mod):
-    """A long plane wave crossing a flat nested patch: inside the patch the nested
-    solution (coarse flux interpolated in, 3x3 mean fed back) stays within 2 % of the
-    amplitude of a single grid at the child's resolution everywhere."""
+def nested_vs_fine(oracle_mod, nest_feedback=0, nest_flux=0):
+    """Largest |eta| difference, inside the patch, between a long plane wave crossing a
+    flat nested patch and the same wave on one grid at the child's resolution; and the
+    wave's amplitude."""
     dxp, h, amp = 300.0, 50.0, 0.05
     npx, npy = 150, 30
     blocks, bathy, man = nested_flat(dxp, h, npx=npx, npy=npy, cx=60, cw=30, cy=6, ch=18,
@@ -345,7 +347,8 @@ def test_nested_plane_wave_matches_fine_grid(oracle_mod):
     def wave(x):
         return amp * np.exp(-((x - x0) / (lam / 4)) ** 2)
 
-    o = oracle_mod.Oracle(blocks, bathy, man, dt=dt)
+    o = oracle_mod.Oracle(blocks, bathy, man, dt=dt, nest_feedback=nest_feedback,
+                          nest_flux=nest_flux)
     xp = centres(npx, dxp)
     xfp = np.arange(npx + 1) * dxp
     o.set_state(0, eta=np.tile(wave(xp), (npy, 1)), M=np.tile(c * wave(xfp), (npy, 1)))
@@ -364,7 +367,98 @@ def test_nested_plane_wave_matches_fine_grid(oracle_mod):
         ec = o.get_state(1)[0]
         ef = f.get_state(0)[0][18:18 + 54, 180:180 + 90]
         worst = max(worst, np.abs(ec - ef).max())
+    return worst, amp
+
+
+def test_nested_plane_wave_matches_fine_grid(oracle_mod):
+    """A long plane wave crossing a flat nested patch: inside the patch the nested
+    solution (coarse flux interpolated in, 3x3 mean fed back) stays within 2 % of the
+    amplitude of a single grid at the child's resolution everywhere."""
+    worst, amp = nested_vs_fine(oracle_mod)
     assert worst <= 0.02 * amp
+
+
+# ------------------------------------ nesting options: full feedback (R8), constant flux (R7)
+@pytest.mark.parametrize("fb,fl", [(1, 0), (0, 1), (1, 1)])
+def test_lake_at_rest_nested_bitwise_with_options(oracle_mod, fb, fl):
+    test_lake_at_rest_nested_bitwise(oracle_mod, nest_feedback=fb, nest_flux=fl, steps=2000)
+
+
+@pytest.mark.parametrize("fb,fl", [(1, 0), (0, 1), (1, 1)])
+def test_nested_budget_closes_with_options(oracle_mod, fb, fl):
+    test_nested_budget_closes(oracle_mod, nest_feedback=fb, nest_flux=fl)
+
+
+@pytest.mark.parametrize("fb,fl", [(1, 0), (0, 1), (1, 1)])
+def test_nested_plane_wave_matches_fine_grid_with_options(oracle_mod, fb, fl):
+    """Every nesting option keeps the nested wave within 2 % of the fine-grid wave."""
+    worst, amp = nested_vs_fine(oracle_mod, nest_feedback=fb, nest_flux=fl)
+    assert worst <= 0.02 * amp
+
+
+def test_full_feedback_sets_every_covered_cell_to_the_child_mean(oracle_mod):
+    """Full two-way nesting. (i) A constant child field averages to itself within one ulp
+    on every covered parent cell, not just the ring. (ii) A pulse over a flat two-level
+    nest: after each step every covered parent cell equals the mean of its 3x3 child
+    cells (all wet; with two levels the child's levels after the step are the values
+    that were averaged) to rounding, while with ring feedback the inner cells keep
+    values of their own."""
+    blocks, bathy, man = nested_flat()
+    I0, J0, a, b = 30, 6, 30, 18
+    o = oracle_mod.Oracle(blocks, bathy, man, dt=2.0, nest_feedback=oracle_mod.NEST_FULL)
+    cval = 0.123456789
+    o.set_state(1, eta=np.full((54, 90), cval))
+    o.step(1)
+    e = o.get_state(0)[0]
+    assert np.all(np.abs(e[J0:J0 + b, I0:I0 + a] - cval) <= np.spacing(cval))
+    assert o.budget(0)["ring"] > 0
+
+    def pulse(x, y, cx, cy):
+        return 0.2 * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * 1500.0 ** 2))
+
+    dxp = blocks[0]["dx"]
+    xp, yp = np.meshgrid(centres(90, dxp), centres(30, dxp))
+    xc, yc = np.meshgrid(I0 * dxp + centres(90, dxp / 3), J0 * dxp + centres(54, dxp / 3))
+    cx, cy = (I0 + 12) * dxp, (J0 + 7) * dxp
+    gaps = {}
+    for fb in (oracle_mod.NEST_RING, oracle_mod.NEST_FULL):
+        o = oracle_mod.Oracle(blocks, bathy, man, dt=2.0, nest_feedback=fb)
+        o.set_state(0, eta=pulse(xp, yp, cx, cy))
+        o.set_state(1, eta=pulse(xc, yc, cx, cy))
+        gap = 0.0
+        for _ in range(20):
+            o.step(1)
+            ep, ec = o.get_state(0)[0], o.get_state(1)[0]
+            mean = ec.reshape(b, 3, a, 3).mean(axis=(1, 3))
+            cover = ep[J0:J0 + b, I0:I0 + a]
+            if fb == oracle_mod.NEST_FULL:
+                assert np.all(np.abs(cover - mean) <= 4 * np.spacing(np.abs(mean).max()))
+            gap = max(gap, np.abs(cover - mean)[1:-1, 1:-1].max())
+        gaps[fb] = gap
+    assert gaps[oracle_mod.NEST_RING] > 1e-6  # the ring option leaves the inner cells alone
+
+
+def test_constant_flux_gives_each_fine_face_its_coarse_face(oracle_mod):
+    """Piecewise-constant coarse-to-fine flux on steady shear flow M(y) = a + b y: each
+    fine face of a child edge carries exactly the parent flux of the coarse face it lies
+    on, so the edge passes exactly the coarse discharge (3 fine faces of dx/3 each)."""
+    blocks, bathy, man = nested_flat(bc=(0, 0, 0, 0))
+    o = oracle_mod.Oracle(blocks, bathy, man, dt=2.0, nest_flux=oracle_mod.FLUX_CONSTANT)
+    dxp = blocks[0]["dx"]
+    yp = centres(30, dxp)
+    Mp = np.tile((0.3 + 2e-5 * yp)[:, None], (1, 91))
+    Mp[:, 0] = Mp[:, -1] = 0.0
+    o.set_state(0, M=Mp)
+    o.step(1)
+    P = o.get_state(0)[1]
+    Mc = o.get_state(1)[1]
+    I0, J0 = blocks[1]["i0"], blocks[1]["j0"]
+    for f, F in ((0, I0), (90, I0 + 30)):
+        coarse = P[J0:J0 + 18, F]
+        assert np.array_equal(Mc[:, f], np.repeat(coarse, 3))
+        fine_q = Mc[:, f].reshape(18, 3).sum(axis=1) * (dxp / 3)
+        assert np.allclose(fine_q, coarse * dxp, rtol=1e-15, atol=0)
+    assert not np.allclose(np.diff(Mc[3:-3, 0]), 0.0)  # the profile is really sheared
 
 
 # ------------------------------------------------------------------------- outputs (R9)
@@ -481,3 +575,59 @@ def test_max_velocity_is_zero_at_rest_and_on_dry_land_and_grows_monotonically(or
         prev = cur
     never_wet = np.isnan(o.max_height(0))
     assert prev.max() > 0.01 and never_wet.any() and np.all(prev[never_wet] == 0.0)
+
+
+def pulse_nested_vs_fine(oracle_mod, nest_feedback, nest_flux, dxp=300.0, h=50.0, amp=0.1):
+    """A Gaussian pulse (sigma 1.5 km) spreads from outside a flat 2-level nest into the
+    child (30 x 30 parent cells, dx 100 m) and is compared, every 20 s for 400 s, with
+    the same pulse on one grid at 100 m. Returns the largest |eta| differences in the
+    child, on the parent cells the child covers (against the fine grid's 3 x 3 means)
+    and on the other parent cells, each over the amplitude."""
+    npx, npy, I0, J0, cw = 90, 60, 36, 15, 30
+
+    def pulse(x, y):
+        return amp * np.exp(-((x - 20 * dxp) ** 2 + (y - 30 * dxp) ** 2) / (2 * 1500.0 ** 2))
+
+    blocks = [dict(level=1, parent=-1, nx=npx, ny=npy, i0=0, j0=0, dx=dxp, bc=(1, 1, 1, 1)),
+              dict(level=2, parent=0, nx=3 * cw, ny=3 * cw, i0=I0, j0=J0, dx=dxp / 3,
+                   bc=(0,) * 4)]
+    bathy = [np.full((npy, npx), h), np.full((3 * cw, 3 * cw), h)]
+    man = [np.zeros((npy, npx), np.float32), np.zeros((3 * cw, 3 * cw), np.float32)]
+    o = oracle_mod.Oracle(blocks, bathy, man, dt=2.0, nest_feedback=nest_feedback,
+                          nest_flux=nest_flux)
+    xp, yp = np.meshgrid(centres(npx, dxp), centres(npy, dxp))
+    xc, yc = np.meshgrid(I0 * dxp + centres(3 * cw, dxp / 3), J0 * dxp + centres(3 * cw, dxp / 3))
+    o.set_state(0, eta=pulse(xp, yp))
+    o.set_state(1, eta=pulse(xc, yc))
+    blk, hh, nn = single(3 * npx, 3 * npy, dxp / 3, h, bc=(1, 1, 1, 1))
+    f = oracle_mod.Oracle([blk], [hh], [nn], dt=2.0)
+    xf, yf = np.meshgrid(centres(3 * npx, dxp / 3), centres(3 * npy, dxp / 3))
+    f.set_state(0, eta=pulse(xf, yf))
+    cov = (slice(J0, J0 + cw), slice(I0, I0 + cw))
+    out = np.ones((npy, npx), bool)
+    out[cov] = False
+    err = np.zeros(3)
+    for _ in range(20):
+        o.step(10)
+        f.step(10)
+        ef = f.get_state(0)[0]
+        efc = ef.reshape(npy, 3, npx, 3).mean(axis=(1, 3))
+        ep, ec = o.get_state(0)[0], o.get_state(1)[0]
+        err = np.maximum(err, [np.abs(ec - ef[3 * J0:3 * (J0 + cw), 3 * I0:3 * (I0 + cw)]).max(),
+                               np.abs(ep[cov] - efc[cov]).max(), np.abs(ep[out] - efc[out]).max()])
+    return err / amp
+
+
+def test_nested_pulse_vs_fine_grid_for_every_option(oracle_mod):
+    """Nested against single-fine-grid accuracy for the four nesting options. Every one
+    keeps the child within 1 % of the amplitude; full feedback brings the covered parent
+    cells to the child's accuracy (ring feedback leaves them at the coarse grid's); the
+    parent cells outside are the coarse grid's own error under every option."""
+    e = {(fb, fl): pulse_nested_vs_fine(oracle_mod, fb, fl) for fb in (0, 1) for fl in (0, 1)}
+    for v in e.values():
+        assert v[0] <= 0.01
+    for fl in (0, 1):
+        assert e[(1, fl)][1] < 0.85 * e[(0, fl)][1]
+        assert e[(1, fl)][1] <= 1.1 * e[(1, fl)][0]
+    outside = [v[2] for v in e.values()]
+    assert max(outside) - min(outside) <= 1e-3 * max(outside)
