@@ -54,12 +54,22 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--tile", type=int, nargs=2, default=(0, 0), help="strip shape (0 0 = default)")
+    ap.add_argument("--nest-feedback", choices=("ring", "full"), default="ring",
+                    help="fine-to-coarse feedback on the boundary ring or every covered cell")
+    ap.add_argument("--nest-flux", choices=("linear", "constant"), default="linear",
+                    help="coarse-to-fine edge flux")
+    ap.add_argument("--track-velocity", action="store_true",
+                    help="keep the maximum water velocity in the timed runs")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-n", type=int, default=30, help="requests in the serving trace")
     ap.add_argument("--serve-scale", type=float, default=1.0 / 60.0,
                     help="time scale of the serving trace (arrivals and durations)")
     ap.add_argument("--serve-pool-gb", type=int, default=32)
+    ap.add_argument("--serve-audit-every", type=int, default=10,
+                    help="run every N-th request again in FP64 after the trace (0: no audit)")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--accuracy-c4-steps", type=int, default=0,
+                    help="also compare FP32 with FP64 on the 46.65 M-cell workload over N steps")
     ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
@@ -177,11 +187,19 @@ def workload():
     return scenarios.config4(steps=SIX_HOURS_STEPS)
 
 
-def time_device(rti, sc, precision, steps, warmup, schedule, world, tile=(0, 0)):
+def handle_options(a):
+    """Handle keywords of the run's nesting and output options."""
+    return dict(nest_feedback=1 if a.nest_feedback == "full" else 0,
+                nest_flux=1 if a.nest_flux == "constant" else 0,
+                track_velocity=bool(a.track_velocity))
+
+
+def time_device(rti, sc, precision, steps, warmup, schedule, world, tile=(0, 0), opts=None):
     """Kernel-only rate: inputs resident in HBM, CUDA events on the launching stream."""
     import torch
 
-    h = rti.Handle.from_scenario(sc, precision=precision, schedule=schedule, tile=tuple(tile))
+    h = rti.Handle.from_scenario(sc, precision=precision, schedule=schedule, tile=tuple(tile),
+                                 **(opts or {}))
     stream = torch.cuda.Stream()
     h.step(warmup, stream)
     h.sync()
@@ -199,22 +217,41 @@ def time_device(rti, sc, precision, steps, warmup, schedule, world, tile=(0, 0))
     return ms
 
 
+def pinned_like(a, torch):
+    """A page-locked host copy of numpy array `a` (made outside any timed region)."""
+    import numpy as np
+
+    dt = {np.dtype(np.float64): torch.float64, np.dtype(np.float32): torch.float32}[a.dtype]
+    out = torch.empty(a.shape, dtype=dt, pin_memory=True).numpy()
+    out[...] = a
+    return out
+
+
 def time_e2e(rti, sc, steps, world):
-    """The same rate through the public API with host buffers: create (bathymetry and
-    Manning n copied in), initial uplift, the steps, and the forecast outputs (max depth
-    and arrival time of every block) copied back, all inside the timed region."""
+    """The same rate through the public API with host buffers in pinned memory: create
+    (bathymetry and Manning n copied in), initial uplift, the steps, and the forecast
+    outputs (max depth and arrival time of every block) copied back into the caller's
+    arrays, all inside the timed region."""
     import numpy as np
     import torch
 
-    outs = [(np.empty((b["ny"], b["nx"])), np.empty((b["ny"], b["nx"]))) for b in sc.blocks]
+    bathy = [pinned_like(np.asarray(x, np.float64), torch) for x in sc.bathy]
+    man = [pinned_like(np.asarray(x, np.float32), torch) for x in sc.manning]
+    dz = [None if u is None else pinned_like(np.asarray(u, np.float64), torch) for u in sc.uplift]
+    outs = [(pinned_like(np.zeros((b["ny"], b["nx"])), torch),
+             pinned_like(np.zeros((b["ny"], b["nx"])), torch)) for b in sc.blocks]
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = rti.Handle.from_scenario(sc, precision=rti.FP32)
+    h = rti.Handle(sc.blocks, bathy, man, sc.dt, sc.g, sc.dry_eps, sc.arrival_thr,
+                   precision=rti.FP32)
+    for k, u in enumerate(dz):
+        if u is not None:
+            h.set_initial_uplift(k, u)
     h.step(steps)
     for k, (md, at) in enumerate(outs):
-        md[...] = h.max_depth(k)
-        at[...] = h.arrival_time(k)
+        h.max_depth(k, out=md)
+        h.arrival_time(k, out=at)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     h2d, d2h = h.transfer_bytes()
@@ -237,7 +274,7 @@ def serving(rti, sc5, a, world):
     trace = S.poisson_trace(seed=2024, n=a.serve_n, mean_s=20.0)
     barrier(world)
     srv = serve.Server(sites, pool_bytes=a.serve_pool_gb << 30, precision=rti.FP32,
-                       chunk_steps=50)
+                       chunk_steps=50, audit_every=a.serve_audit_every or None)
     reqs, st = srv.run(trace, time_scale=a.serve_scale, max_wall_s=180.0)
     srv.close()
     del srv
@@ -262,6 +299,7 @@ def serving(rti, sc5, a, world):
     return {"scenarios_per_h": st["scenarios_per_h"], "p50_s": st["p50_s"], "p99_s": st["p99_s"],
             "mean_s": st["mean_s"], "completed": st["completed"], "requests": st["requests"],
             "max_live": st["max_live"], "gcups": st["gcups"], "precision": "fp32",
+            "fp64_audit": st["audit"],
             "trace": f"{a.serve_n} Poisson arrivals (mean 20 s), 3/4/5-level uniform, "
                      f"1-6 h; arrivals and durations x{a.serve_scale:.4g}; "
                      f"HBM pool {a.serve_pool_gb} GB; chunk 50 steps",
@@ -304,19 +342,20 @@ def batch_c3(rti, steps=200, warmup=5):
     return out
 
 
-def accuracy(rti):
-    """FP32 against the FP64 path (which matches the FP64 oracle to 1e-12) on the 3-level
-    C2 nest over its full hour: max |eta| and max-height error (m), wet/dry mismatch (%
-    of cells, final state and ever-wet), arrival-time error (s)."""
+def accuracy(rti, sc=None, steps=None):
+    """FP32 against the FP64 path (which matches the FP64 oracle to 1e-12), by default on
+    the 3-level C2 nest over its full hour: max |eta| and max-height error (m), wet/dry
+    mismatch (% of cells, final state and ever-wet), arrival-time error (s; max, p99,
+    mean)."""
     import numpy as np
 
     from paper_2408_07609_gb300 import scenarios as S
 
-    sc = S.config2()
-    out = {}
+    sc = S.config2() if sc is None else sc
+    steps = sc.steps if steps is None else steps
     hs = {p: rti.Handle.from_scenario(sc, precision=p) for p in (rti.FP32, rti.FP64)}
     for h in hs.values():
-        h.step(sc.steps)
+        h.step(steps)
     e_eta = e_max = 0.0
     mis_wet = mis_ever = n = 0
     arr_err, arr_mis = [], 0
@@ -338,11 +377,13 @@ def accuracy(rti):
     for h in hs.values():
         h.close()
     ae = np.concatenate(arr_err)
-    return {"workload": sc.name, "against": "FP64 GPU path", "steps": sc.steps,
+    return {"workload": sc.name, "against": "FP64 GPU path", "steps": steps,
             "max_abs_eta_m": e_eta, "max_abs_max_height_m": e_max,
             "wet_dry_mismatch_pct": 100.0 * mis_wet / n, "ever_wet_mismatch_pct": 100.0 * mis_ever / n,
             "arrival_max_err_s": float(ae.max()) if ae.size else 0.0,
             "arrival_mean_err_s": float(ae.mean()) if ae.size else 0.0,
+            "arrival_p99_err_s": float(np.percentile(ae, 99)) if ae.size else 0.0,
+            "arrived_cells": int(ae.size),
             "arrival_mismatch_cells": arr_mis}
 
 
@@ -370,17 +411,19 @@ def run_ours(a):
     cells = sc.cells
     fp32_bytes = rti.footprint(sc.blocks, rti.make_params(sc.dt, precision=rti.FP32))
     with Clocks(local) as clk:
-        ms32 = time_device(rti, sc, rti.FP32, a.steps, a.warmup, a.schedule, world, a.tile)
+        ms32 = time_device(rti, sc, rti.FP32, a.steps, a.warmup, a.schedule, world, a.tile,
+                           handle_options(a))
     clocks = clk.summary()
     ms32 = max_over_ranks(ms32, world)
     ms64 = time_device(rti, sc, rti.FP64, a.fp64_steps, max(3, a.warmup // 2), a.schedule, world,
-                       a.tile)
+                       a.tile, handle_options(a))
     ms64 = max_over_ranks(ms64, world)
     per32, per64 = ms32 / a.steps, ms64 / a.fp64_steps
     gcups32 = whole_job_rate(cells, a.steps, ms32, world)
     gcups64 = whole_job_rate(cells, a.fp64_steps, ms64, world)
     peak, kind = peaks()
-    bpc = BYTES_PER_CELL_STEP["f32"]
+    bpc = BYTES_PER_CELL_STEP["f32"] + (4 if a.track_velocity else 0)  # + max-speed plane read
+    default_run = (a.nest_feedback, a.nest_flux, a.track_velocity) == ("ring", "linear", False)
     achieved = bpc * cells * a.steps / (ms32 / 1e3) / 1e9  # GB/s of one launch of K steps
     e2e = None
     if not a.no_e2e:
@@ -389,9 +432,11 @@ def run_ours(a):
         e2e = {"value": world * cells * a.steps / wall / 1e9, "unit": "GCUPS",
                "h2d_bytes_per_step": h2d // a.steps, "d2h_bytes_per_step": d2h // a.steps,
                "includes": "create (bathymetry, Manning n), initial uplift, steps, max depth "
-                           "and arrival of every block read back"}
+                           "and arrival of every block read back; host arrays in pinned "
+                           "memory"}
     srv = None if a.no_serving else serving(rti, sc, a, world)
     acc = None if (a.no_accuracy or rank != 0) else accuracy(rti)
+    acc4 = None if (not a.accuracy_c4_steps or rank != 0) else accuracy(rti, sc, a.accuracy_c4_steps)
     c3 = None if a.no_batch else batch_c3(rti)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -411,6 +456,8 @@ def run_ours(a):
                        "levels": 5, "dt_s": sc.dt, "precision": "fp32",
                        "schedule": "persistent" if a.schedule == 0 else "one launch per step",
                        "strip": list(a.tile) if a.tile[0] else [28, 64],
+                       "nesting": f"{a.nest_feedback} feedback, {a.nest_flux} edge flux",
+                       "max_velocity": bool(a.track_velocity),
                        "l2": f"working set {fp32_bytes / 1e9:.2f} GB (fp32) > 129 MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "fp64": {"value": gcups64, "unit": "GCUPS", "ms_per_step": per64,
@@ -423,15 +470,18 @@ def run_ours(a):
             "gpu_launches": 3 if a.schedule == 0 else a.steps + 2,
             "serving": srv,
             "fp32_accuracy": acc,
+            "fp32_accuracy_c4": acc4,
             "batch_c3": c3,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (None if NCU_F32_DRAM_BYTES_PER_CELL_STEP is None else
+                         "traffic": (None if NCU_F32_DRAM_BYTES_PER_CELL_STEP is None
+                                     or not default_run else
                                      NCU_F32_DRAM_BYTES_PER_CELL_STEP * cells * a.steps),
                          "traffic_note": "bytes per launch of the timed K steps, scaled from "
                                          "a single-step ncu capture of the 4-level case",
                          "peak_kind": f"{kind} hbm_gbs",
-                         "bytes_per_cell_step": bpc, "kernel": "k_step<float>"},
+                         "bytes_per_cell_step": bpc,
+                         "kernel": f"k_step<float, {'true' if a.track_velocity else 'false'}>"},
             "cpu_baseline": cpu,
             "clocks": clocks,
         })

@@ -215,23 +215,28 @@ class Handle:
         p = lambda a: None if a is None else a.ctypes.data_as(_dp)
         self._chk(lib().rti_set_state(self._h, k, p(eta), p(M), p(N)), "set_state")
 
-    def _field(self, fn, k):
+    def _field(self, fn, k, out=None):
+        """out: a C-contiguous (ny, nx) float64 array to fill (e.g. pinned host memory);
+        None allocates one."""
         ny, nx = self.shape(k)
-        out = np.empty((ny, nx))
+        if out is None:
+            out = np.empty((ny, nx))
+        elif out.shape != (ny, nx) or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a C-contiguous ({ny}, {nx}) float64 array")
         self._chk(getattr(lib(), fn)(self._h, k, out.ctypes.data_as(_dp)), fn)
         return out
 
-    def max_depth(self, k):
-        return self._field("rti_get_max_depth", k)
+    def max_depth(self, k, out=None):
+        return self._field("rti_get_max_depth", k, out)
 
-    def max_height(self, k):
-        return self._field("rti_get_max_height", k)
+    def max_height(self, k, out=None):
+        return self._field("rti_get_max_height", k, out)
 
-    def arrival_time(self, k):
-        return self._field("rti_get_arrival_time", k)
+    def arrival_time(self, k, out=None):
+        return self._field("rti_get_arrival_time", k, out)
 
-    def max_velocity(self, k):
-        return self._field("rti_get_max_velocity", k)
+    def max_velocity(self, k, out=None):
+        return self._field("rti_get_max_velocity", k, out)
 
     def budget(self, k):
         out = np.empty(4)

@@ -13,6 +13,10 @@ the host.
 The pool is one caller-owned device allocation (a torch uint8 tensor) carved first-fit
 into 256-byte aligned arenas, so admission and retirement allocate nothing on the
 device and never stall the running batch.
+
+Audit: with audit_every = N, every N-th request (by arrival) is run again in binary64
+once the trace is served, off the forecast path, and its forecast outputs (maximum
+height and arrival time of every block) are compared with the binary32 forecast.
 """
 from __future__ import annotations
 
@@ -81,6 +85,8 @@ class Request:
     admitted_s: float = float("nan")
     done_s: float = float("nan")
     result: dict = field(default_factory=dict)
+    fields: dict = field(default_factory=dict)  # kept for the audit: block -> (max h, arrival)
+    audit: dict = field(default_factory=dict)
 
     @property
     def latency_s(self) -> float:
@@ -94,13 +100,15 @@ def load_sites(kinds=("3level", "4level", "5level"), seed=1000):
 
 class Server:
     def __init__(self, sites: dict, pool_bytes: int, precision=rti.FP32, chunk_steps: int = 50,
-                 schedule=rti.SCHED_PERSISTENT, keep_fields: bool = False):
+                 schedule=rti.SCHED_PERSISTENT, keep_fields: bool = False,
+                 audit_every: int | None = None):
         import torch
 
         self.torch = torch
         self.sites = sites
         self.prec = precision
         self.keep = keep_fields
+        self.audit_every = audit_every
         self.pool = Pool(pool_bytes, torch.empty(int(pool_bytes), dtype=torch.uint8,
                                                  device="cuda"))
         self.batch = rti.Batch(precision, schedule, chunk_steps)
@@ -118,10 +126,15 @@ class Server:
         live[req.rid] = (req, h, off)
         return True
 
+    def _audited(self, req: Request) -> bool:
+        return bool(self.audit_every) and req.rid % self.audit_every == 0
+
     def _retire(self, req: Request, h: rti.Handle, off: int, t0: float):
         out = {}
         for k in range(len(h.blocks)):
             mh, at = h.max_height(k), h.arrival_time(k)
+            if self._audited(req):
+                req.fields[k] = (mh, at)
             if self.keep:
                 out[k] = (mh, at)
             else:
@@ -134,11 +147,38 @@ class Server:
         h.close()
         self.pool.release(off)
 
+    def _audit(self, req: Request):
+        """Run `req` again in binary64 in the pool and compare its forecast outputs."""
+        site = self.sites[req.kind]
+        sc = S.with_new_source(site, req.seed)
+        p = rti.make_params(site.dt, site.g, site.dry_eps, site.arrival_thr, rti.FP64)
+        off = self.pool.alloc(rti.footprint(site.blocks, p))
+        if off is None:
+            raise MemoryError(f"audit of request {req.rid} does not fit the pool")
+        h = rti.Handle.from_scenario(sc, precision=rti.FP64, device_mem=self.pool.view(off))
+        h.step(req.nsteps)
+        d_max, d_arr, mis = 0.0, 0.0, 0
+        for k in range(len(h.blocks)):
+            mh, at = h.max_height(k), h.arrival_time(k)
+            mh32, at32 = req.fields[k]
+            both = ~np.isnan(mh) & ~np.isnan(mh32)
+            if both.any():
+                d_max = max(d_max, float(np.abs(mh[both] - mh32[both]).max()))
+            mis += int((np.isnan(mh) != np.isnan(mh32)).sum() + ((at >= 0) != (at32 >= 0)).sum())
+            ab = (at >= 0) & (at32 >= 0)
+            if ab.any():
+                d_arr = max(d_arr, float(np.abs(at[ab] - at32[ab]).max()))
+        h.close()
+        self.pool.release(off)
+        req.fields = {}
+        req.audit = dict(max_height_err_m=d_max, arrival_err_s=d_arr, mismatched_cells=mis)
+
     def run(self, trace, time_scale: float = 1.0, max_wall_s: float | None = None,
             admit_per_chunk: int | None = None):
         """Serve `trace` (dicts with arrival_s, kind, seed, hours); arrival times and
         simulated durations are multiplied by time_scale. At most admit_per_chunk
-        requests join between two chunks (None: all that have arrived and fit).
+        requests join between two chunks (None: all that have arrived and fit). The
+        binary64 audit of the sampled requests follows the trace.
         Returns (requests, stats)."""
         reqs = []
         for i, t in enumerate(trace):
@@ -187,6 +227,16 @@ class Server:
                 time.sleep(max(0.0, min(0.05, pending[0].arrival_s - (time.perf_counter() - t0))))
         wall = time.perf_counter() - t0
         done = [r for r in reqs if np.isfinite(r.done_s)]
+        ta = time.perf_counter()
+        audited = [r for r in done if self._audited(r)]
+        for r in audited:
+            self._audit(r)
+        audit = None
+        if audited:
+            audit = dict(requests=len(audited), wall_s=time.perf_counter() - ta,
+                         max_height_err_m=max(r.audit["max_height_err_m"] for r in audited),
+                         arrival_err_s=max(r.audit["arrival_err_s"] for r in audited),
+                         mismatched_cells=sum(r.audit["mismatched_cells"] for r in audited))
         lat = np.array([r.latency_s for r in done]) if done else np.array([float("nan")])
         cell_steps = float(sum(r.cells * r.nsteps for r in done))
         stats = dict(requests=len(reqs), completed=len(done), wall_s=wall,
@@ -194,7 +244,7 @@ class Server:
                      p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
                      mean_s=float(lat.mean()), max_live=max_live, chunks=chunks,
                      gcups=cell_steps / wall / 1e9 if wall > 0 else float("nan"),
-                     time_scale=time_scale)
+                     time_scale=time_scale, audit=audit)
         return reqs, stats
 
     def close(self):

@@ -82,3 +82,33 @@ def test_admission_by_footprint_serialises_when_the_pool_holds_one(rti):
     done = sorted(reqs, key=lambda r: r.done_s)
     assert [r.rid for r in done] == [0, 1, 2, 3]  # admitted in arrival order
     assert all(r.admitted_s >= prev.done_s for prev, r in zip(done, done[1:]))
+
+
+@pytest.mark.gpu
+def test_fp64_audit_sample_checks_the_fp32_forecasts(rti, oracle_mod):
+    """audit_every=2 reruns requests 0 and 2 in binary64 after the trace. The audit's
+    binary64 run is itself the oracle's result (to 1e-12), and the binary32 forecasts it
+    checks stay within the forecast bounds (max height 5 cm)."""
+    from paper_2408_07609_gb300.serve import Server
+
+    sites = {"c1": S.coastal_hierarchy("serving audit 120x96", 4, (120, 96, 1000.0), [],
+                                       dt=1.0, steps=0, shelf_w=20e3, slope_w=30e3,
+                                       source=dict(kind="gauss", sigma=8e3, peak=2.0))}
+    trace = _trace(["c1"] * 3, [0.0, 0.0, 0.0], [11, 12, 13], [150 / 3600] * 3)
+    srv = Server(sites, pool_bytes=1 << 28, precision=rti.FP32, chunk_steps=50, audit_every=2)
+    reqs, stats = srv.run(trace)
+    srv.close()
+    a = stats["audit"]
+    assert a["requests"] == 2 and [bool(r.audit) for r in reqs] == [True, False, True]
+    assert 0 < a["max_height_err_m"] <= 0.05
+    # the audit compares against the binary64 path: recompute request 2's error here
+    r = reqs[2]
+    sc = S.with_new_source(sites["c1"], r.seed)
+    o = oracle_mod.from_scenario(sc)
+    o.step(r.nsteps)
+    h = rti.Handle.from_scenario(sc, precision=rti.FP32)
+    h.step(r.nsteps)
+    g, ref = h.max_height(0), o.max_height(0)
+    both = ~np.isnan(g) & ~np.isnan(ref)
+    assert abs(np.abs(g[both] - ref[both]).max() - r.audit["max_height_err_m"]) <= 1e-9
+    h.close()
