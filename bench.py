@@ -39,7 +39,7 @@ BYTES_PER_CELL_STEP = {"f32": 5 * 4 + 4 + 3 * 4,   # 36
 # dram__bytes_write.sum of one single-step launch on the 7.95 M-cell 4-level hierarchy,
 # divided by its cells); scaled to a launch of the bench by cells x steps. Set to None
 # whenever the kernel changes until it is captured again.
-NCU_F32_DRAM_BYTES_PER_CELL_STEP = (228.228864e6 + 80.555008e6) / 7.95e6  # 38.8 B
+NCU_F32_DRAM_BYTES_PER_CELL_STEP = (229.652992e6 + 83.252480e6) / 7.95e6  # 39.4 B
 
 
 def parse():

@@ -173,12 +173,15 @@ struct Group {
   size_t cap_kids = 0;
   Tile* d_tiles = nullptr;
   size_t cap_tiles = 0;
-  int* d_counts = nullptr;  // [0] = ntiles, [1] = nscen
+  int* d_counts = nullptr;  // [0] = ntiles, [1] = nscen, [2] = full-feedback items
+  FbItem* d_fb = nullptr;
+  size_t cap_fb = 0;
+  int nfb = 0;
   ScenDev* d_scen = nullptr;
   size_t cap_scen = 0;
   int* d_status = nullptr;
   Bar* d_bar = nullptr;
-  int grid = 0, grid_track = 0;  // co-resident grids of the two kernel variants
+  int grid = 0, grid_track = 0, grid_fb = 0;  // co-resident grids of the kernel variants
   bool track = false;            // some member keeps the maximum velocity
   long long spin_cycles = kSpinCycles;
   // pinned staging for table uploads
@@ -295,6 +298,7 @@ void free_group_dev(Group* g) {
   cudaFree(g->d_kids);
   cudaFree(g->d_tiles);
   cudaFree(g->d_counts);
+  cudaFree(g->d_fb);
   cudaFree(g->d_scen);
   cudaFree(g->d_status);
   cudaFree(g->d_bar);
@@ -305,6 +309,7 @@ void free_group_dev(Group* g) {
   g->d_kids = nullptr;
   g->d_tiles = nullptr;
   g->d_counts = nullptr;
+  g->d_fb = nullptr;
   g->d_scen = nullptr;
   g->d_status = nullptr;
   g->d_bar = nullptr;
@@ -319,10 +324,10 @@ int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, std::st
   g->tx = tx;
   g->ty = ty;
   g->chunk = chunk;
-  cudaError_t e = cudaMalloc(&g->d_counts, 2 * sizeof(int));
+  cudaError_t e = cudaMalloc(&g->d_counts, 3 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_bar, sizeof(Bar));
-  if (e == cudaSuccess) e = cudaMemset(g->d_counts, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->d_counts, 0, 3 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->d_bar, 0, sizeof(Bar));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->staged, cudaEventDisableTiming);
@@ -332,11 +337,14 @@ int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, std::st
     if (c > 0) g->spin_cycles = c;
   }
   if (e == cudaSuccess) {
-    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid, tx, ty, false)
-                         : persistent_grid<double>(&g->grid, tx, ty, false);
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid, tx, ty, kStepPlain)
+                         : persistent_grid<double>(&g->grid, tx, ty, kStepPlain);
   if (e == cudaSuccess)
-    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_track, tx, ty, true)
-                         : persistent_grid<double>(&g->grid_track, tx, ty, true);
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_track, tx, ty, kStepTrack)
+                         : persistent_grid<double>(&g->grid_track, tx, ty, kStepTrack);
+  if (e == cudaSuccess)
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_fb, tx, ty, kStepFeedback)
+                         : persistent_grid<double>(&g->grid_fb, tx, ty, kStepFeedback);
   }
   if (e != cudaSuccess) return cuda_err(err, e, "group setup");
   return RTI_OK;
@@ -349,6 +357,9 @@ KParams<T> kparams(Group* g, int nsteps) {
   kp.kids = g->d_kids;
   kp.tiles = g->d_tiles;
   kp.ntiles = g->d_counts;
+  kp.fb = g->d_fb;
+  kp.nfb = g->d_counts + 2;
+  kp.fb_any = g->nfb > 0 ? 1 : 0;
   kp.scen = g->d_scen;
   kp.status = g->d_status;
   kp.bar = g->d_bar;
@@ -385,6 +396,7 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   std::vector<Blk<T>> blks;
   std::vector<int> kids;
   std::vector<Tile> tiles;
+  std::vector<FbItem> fb;
   long long cells = 0;
   bool track = false;
   for (size_t mi = 0; mi < g->members.size(); ++mi) {
@@ -399,6 +411,15 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
       const int cf = (int)kids.size();
       for (int c : ch[k]) kids.push_back(base + c);
       blks.push_back(make_blk<T>(h, k, base, (int)mi, cf, (int)ch[k].size(), g->tx));
+    }
+    if (h->params.nest_feedback == RTI_NEST_FULL) {  // every covered cell, 32 per item
+      for (int c = 0; c < nb; ++c) {
+        const rti_block& cd = h->blocks[c];
+        if (cd.parent < 0) continue;
+        for (int J = cd.j0; J < cd.j0 + cd.ny / 3; ++J)
+          for (int I0 = cd.i0; I0 < cd.i0 + cd.nx / 3; I0 += 32)
+            fb.push_back(FbItem{base + cd.parent, base + c, J, I0});
+      }
     }
     for (int k = 0; k < nb; ++k) {
       const rti_block& d = h->blocks[k];
@@ -444,9 +465,11 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   if (e == cudaSuccess) e = grow(&g->d_tiles, &g->cap_tiles, tiles.size() * sizeof(Tile) + 64, &moved);
   if (e == cudaSuccess)
     e = grow(&g->d_scen, &g->cap_scen, g->members.size() * sizeof(ScenDev) + 64, &moved);
+  if (e == cudaSuccess) e = grow(&g->d_fb, &g->cap_fb, fb.size() * sizeof(FbItem) + 64, &moved);
   if (e != cudaSuccess) return cuda_err(err, e, "device tables");
-  // the captured graph holds the old pointers, or the other kernel variant
-  if ((moved || track != g->track) && g->gexec) {
+  // the captured graph holds the old pointers, the other kernel variant, or launches
+  // with or without the feedback phase
+  if ((moved || track != g->track || fb.empty() != (g->nfb == 0)) && g->gexec) {
     cudaGraphExecDestroy(g->gexec);
     g->gexec = nullptr;
     g->graph_tried = false;
@@ -455,8 +478,9 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   const size_t nb_kids = kids.size() * sizeof(int);
   const size_t nb_tiles = tiles.size() * sizeof(Tile);
   const size_t nb_scen = g->members.size() * sizeof(ScenDev);
+  const size_t nb_fb = fb.size() * sizeof(FbItem);
   const size_t need = align256(nb_blk) + align256(nb_kids) + align256(nb_tiles) +
-                      align256(nb_scen) + 256;
+                      align256(nb_scen) + align256(nb_fb) + 256;
   // the previous upload must have left the staging buffer before it is rewritten
   e = cudaEventSynchronize(g->staged);
   if (e != cudaSuccess) return cuda_err(err, e, "staging wait");
@@ -481,11 +505,12 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
     sc[mi].base = g->members[mi]->base;
     sc[mi].remaining = g->remaining[mi];
   }
-  int counts[2] = {(int)tiles.size(), (int)g->members.size()};
+  int counts[3] = {(int)tiles.size(), (int)g->members.size(), (int)fb.size()};
   e = put(blks.data(), nb_blk, g->d_blk);
   if (e == cudaSuccess) e = put(kids.data(), nb_kids, g->d_kids);
   if (e == cudaSuccess) e = put(tiles.data(), nb_tiles, g->d_tiles);
   if (e == cudaSuccess) e = put(sc.data(), nb_scen, g->d_scen);
+  if (e == cudaSuccess) e = put(fb.data(), nb_fb, g->d_fb);
   if (e == cudaSuccess) e = put(counts, sizeof(counts), g->d_counts);
   if (e == cudaSuccess) e = cudaEventRecord(g->staged, st);
   if (e != cudaSuccess) return cuda_err(err, e, "table upload");
@@ -494,6 +519,7 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   g->nkids = (int)kids.size();
   g->cells = cells;
   g->track = track;
+  g->nfb = (int)fb.size();
   g->dirty = false;
   return RTI_OK;
 }
@@ -502,14 +528,22 @@ int group_upload_any(Group* g, cudaStream_t st, std::string* err) {
   return g->prec == RTI_FP32 ? group_upload<float>(g, st, err) : group_upload<double>(g, st, err);
 }
 
+// grid of the variant a chunk of this group launches (the smallest of the variants a
+// one-launch-per-step chunk uses)
+int launch_grid(const Group* g) {
+  if (g->sched == RTI_SCHED_PERSISTENT)
+    return g->nfb > 0 ? g->grid_fb : (g->track ? g->grid_track : g->grid);
+  return g->track ? g->grid_track : g->grid;
+}
+
 int launch_any(Group* g, int nsteps, cudaStream_t st, std::string* err) {
   cudaError_t e;
   if (g->prec == RTI_FP32)
-    e = launch_chunk<float>(kparams<float>(g, nsteps), g->sched,
-                            g->track ? g->grid_track : g->grid, g->d_counts + 1, st);
+    e = launch_chunk<float>(kparams<float>(g, nsteps), g->sched, launch_grid(g), g->d_counts + 1,
+                            st);
   else
-    e = launch_chunk<double>(kparams<double>(g, nsteps), g->sched,
-                             g->track ? g->grid_track : g->grid, g->d_counts + 1, st);
+    e = launch_chunk<double>(kparams<double>(g, nsteps), g->sched, launch_grid(g),
+                             g->d_counts + 1, st);
   if (e != cudaSuccess) return cuda_err(err, e, "chunk launch");
   return RTI_OK;
 }
@@ -1362,7 +1396,7 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
   k_noalloc_setup<T><<<1, 256, 0, stream>>>(s, b, tx, ty, tiles_x, tiles_y, steps_done, nsteps);
   cudaError_t e = cudaGetLastError();
   int grid = 0;
-  if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty, false);
+  if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty, kStepPlain);
   if (e == cudaSuccess) {
     KParams<T> kp;
     std::memset(&kp, 0, sizeof(kp));

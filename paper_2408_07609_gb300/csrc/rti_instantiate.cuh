@@ -5,17 +5,21 @@
 namespace rti {
 
 template <>
-cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty, bool track) {
+cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty, int mode) {
   (void)tx;
   (void)ty;
   int dev = 0, sms = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = track ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T, true>,
-                                                              kWarps * 32, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T, false>,
-                                                              kWarps * 32, 0);
+    e = mode == kStepFeedback
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T, kStepFeedback>,
+                                                            kWarps * 32, 0)
+        : mode == kStepTrack
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T, kStepTrack>,
+                                                            kWarps * 32, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T, kStepPlain>,
+                                                            kWarps * 32, 0);
   if (e == cudaSuccess) *grid = sms * (per > 0 ? per : 1);
   return e;
 }
@@ -37,12 +41,14 @@ cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = kp.track ? cudaLaunchKernelEx(&cfg, k_step<RTI_T, true>, kp, 0, kp.nsteps)
-                 : cudaLaunchKernelEx(&cfg, k_step<RTI_T, false>, kp, 0, kp.nsteps);
-  } else {  // one launch per step
+    e = kp.fb_any  ? cudaLaunchKernelEx(&cfg, k_step<RTI_T, kStepFeedback>, kp, 0, kp.nsteps)
+        : kp.track ? cudaLaunchKernelEx(&cfg, k_step<RTI_T, kStepTrack>, kp, 0, kp.nsteps)
+                   : cudaLaunchKernelEx(&cfg, k_step<RTI_T, kStepPlain>, kp, 0, kp.nsteps);
+  } else {  // one launch per step (and one for the full-feedback phase before it)
     for (int s = 0; s < kp.nsteps && e == cudaSuccess; ++s) {
-      if (kp.track) k_step<RTI_T, true><<<grid, blk, 0, st>>>(kp, s, 1);
-      else k_step<RTI_T, false><<<grid, blk, 0, st>>>(kp, s, 1);
+      if (kp.fb_any) k_feedback<RTI_T><<<grid, blk, 0, st>>>(kp, s);
+      if (kp.track) k_step<RTI_T, kStepTrack><<<grid, blk, 0, st>>>(kp, s, 1);
+      else k_step<RTI_T, kStepPlain><<<grid, blk, 0, st>>>(kp, s, 1);
       e = cudaGetLastError();
     }
   }

@@ -588,11 +588,9 @@ __device__ __forceinline__ void stage_strip(const KParams<T>& kp, WarpSlot<T>& w
 // Prepass of a strip over the region its march reads: columns x0-2..x0+29, rows
 // y0-2..ye of cells and x-faces, y-faces up to row ye+1. A child's edge faces there get
 // the parent's current fluxes (R7), stored into the child's own level-p arrays, whose
-// edge entries nothing else reads; a parent's ring cells there (every covered cell with
-// full feedback) get their fine-to-coarse eta^{n+1} or "none" (R8) in the ring plane.
-// The means come from the children's own mass step, so with full feedback a cell above
-// a grandchild takes the child's level, as an exchange of every level at once gives.
-// The items of the region are spread over
+// edge entries nothing else reads; a parent's ring cells there get their fine-to-coarse
+// eta^{n+1} or "none" (R8) in the ring plane (with full feedback the feedback phase has
+// filled the plane for every covered cell). The items of the region are spread over
 // the lanes; strips that overlap store the same values, and __syncwarp orders the
 // stores before the march's loads. Kept out of line so that the march's registers do
 // not pay for the nesting arithmetic.
@@ -619,28 +617,21 @@ __device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<
       for (int c = c0 + lane; c < c1; c += 32) b.N[p][ix(b, c, g)] = face_n(b, ws.P, p, c, g);
     }
   }
-  if (td.flags & kTfRing) {
-    const bool full = (b.nest & kNestFull) != 0;
+  if ((td.flags & kTfRing) && !(b.nest & kNestFull)) {  // full feedback: its own phase
     const int c0 = max(cx0, 0), c1 = min(cx1, nx), r0 = max(ry0, 0), r1 = min(ry1, ny);
     for (int q = 0; q < b.child_count; ++q) {
       const Blk<T> ch = RTI_BLK(kp, RTI_KID(kp, b.child_first + q));
       const int a0 = ch.i0, a1 = ch.i0 + ch.nx / 3, b0 = ch.j0, b1 = ch.j0 + ch.ny / 3;
       // the footprint's inner ring within the region: rows b0 and b1-1 (all columns),
-      // columns a0 and a1-1 (rows strictly between); with full feedback, the footprint
-      // within the region, row by row
+      // columns a0 and a1-1 (rows strictly between)
       const int hc0 = max(c0, a0), hc1 = min(c1, a1), nh = max(hc1 - hc0, 0);
       const int vr0 = max(r0, b0 + 1), vr1 = min(r1, b1 - 1), nv = max(vr1 - vr0, 0);
       const bool rb = b0 >= r0 && b0 < r1, rt = b1 - 1 >= r0 && b1 - 1 < r1 && b1 - 1 != b0;
       const bool cl = a0 >= c0 && a0 < c1, cr = a1 - 1 >= c0 && a1 - 1 < c1 && a1 - 1 != a0;
       const int n0 = rb ? nh : 0, n1 = rt ? nh : 0, n2 = cl ? nv : 0, n3 = cr ? nv : 0;
-      const int fr0 = max(r0, b0), nf = max(min(r1, b1) - fr0, 0);
-      const int n = full ? nh * nf : n0 + n1 + n2 + n3;
-      for (int k = lane; k < n; k += 32) {
+      for (int k = lane; k < n0 + n1 + n2 + n3; k += 32) {
         int I, J;
-        if (full) {
-          J = fr0 + k / nh;
-          I = hc0 + (k - (k / nh) * nh);
-        } else if (k < n0) {
+        if (k < n0) {
           I = hc0 + k;
           J = b0;
         } else if (k < n0 + n1) {
@@ -936,9 +927,13 @@ __device__ __forceinline__ bool grid_barrier(Bar* bar, unsigned& gen, int* statu
 // warps take strips from a device counter per step (heavy strips come first in the
 // list), so a slow strip delays no fixed set of others. Counter s & 1 serves step s;
 // the other one is cleared during step s, when no warp can still be taking from it
-// (step s - 1 has ended: a barrier or the previous launch lies between). With more
-// than one step the launch must be cooperative: consecutive steps are separated by the
-// device-wide barrier.
+// (step s - 1 has ended: a barrier or the previous launch lies between). With more than
+// one step the launch must be cooperative: consecutive steps are separated by the
+// device-wide barrier. Variants (kMode): kStepPlain; kStepTrack, whose strips of blocks
+// that keep the maximum velocity take the tracking march; kStepFeedback (cooperative
+// only), which also runs the full-feedback phase of each step, behind one more barrier.
+// A group with full feedback stepped one launch per step runs k_feedback before each
+// kStepPlain or kStepTrack launch instead.
 // Resident CTAs per SM the register allocation targets: binary32 fits 96 registers
 // (5 CTAs of 4 warps) without spilling; binary64 keeps the compiler's choice.
 template <class T>
@@ -950,18 +945,76 @@ struct StepOcc<float> {
   static constexpr int kMinBlocks = 5;
 };
 
-template <class T, bool kAnyTrack>
+// Full-feedback items of step s (R8 on every covered parent cell): items t = w, w + nw,
+// ... of warp w of nw. An item is parent row J, parent cells I0 .. I0 + 31 of one child's
+// footprint; each lane forms the mean of one parent cell from the child's eta^{n+1}
+// recomputed from its level p, into the parent's ring plane, which the parent's strips
+// read once the phase has ended. The descriptors go through the warp's slot (parent in
+// ws.b, child in ws.P), which the strip phase stages again.
+template <class T>
+__device__ __noinline__ void feedback_items(const KParams<T>& kp, WarpSlot<T>& ws, int s,
+                                            int w, int nw) {
+  const int n = *kp.nfb;
+  const int lane = threadIdx.x;
+  int have_p = -1, have_c = -1;
+  for (int t = w; t < n; t += nw) {
+    const FbItem it = kp.fb[t];
+    if (it.blk != have_p) {
+      __syncwarp();
+      warp_copy<T>(&ws.b, &RTI_BLK(kp, it.blk), sizeof(Blk<T>));
+      have_p = it.blk;
+    }
+    if (it.kid != have_c) {
+      __syncwarp();
+      warp_copy<T>(&ws.P, &RTI_BLK(kp, it.kid), sizeof(Blk<T>));
+      have_c = it.kid;
+    }
+    __syncwarp();
+    const Blk<T>& P = ws.b;
+    const Blk<T>& c = ws.P;
+    const ScenDev sc = kp.scen[P.scen];
+    if ((long long)s >= sc.remaining) continue;  // the scenario has finished
+    const int p = (int)((sc.base + s) & 1);
+    const int I = it.I0 + lane;
+    if (I < c.i0 + c.nx / 3) {
+      const size_t o = ix(P, I, it.J);
+      T rv;
+      const bool wet = ring_patch(c, P, p, I - c.i0, it.J - c.j0, P.h[o], rv);
+      P.ring[o] = wet ? rv : ring_none(rv);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) ws.blk = -1;  // the slot no longer holds a strip's descriptors
+  __syncwarp();
+}
+
+// The full-feedback phase of step s as a launch of its own (one launch per step).
+template <class T>
+__global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
+    k_feedback(KParams<T> kp, int s) {
+  __shared__ WarpSlot<T> slots[kWarps];
+  feedback_items(kp, slots[threadIdx.y], s, blockIdx.x * kWarps + threadIdx.y,
+                 gridDim.x * kWarps);
+}
+
+template <class T, int kMode>
 __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
     k_step(KParams<T> kp, int s_first, int s_count) {
+  constexpr bool kAnyTrack = kMode != kStepPlain;
   __shared__ WarpSlot<T> slots[kWarps];
   __shared__ int go;
   WarpSlot<T>& ws = slots[threadIdx.y];
   if (threadIdx.x == 0) ws.blk = -1;
   __syncwarp();
   unsigned gen = 0;
-  if (s_count > 1 && threadIdx.x == 0 && threadIdx.y == 0) gen = ld_acquire_u32(&kp.bar->gen);
+  if ((kMode == kStepFeedback || s_count > 1) && threadIdx.x == 0 && threadIdx.y == 0)
+    gen = ld_acquire_u32(&kp.bar->gen);
   const int nt = *kp.ntiles;
   for (int s = s_first; s < s_first + s_count; ++s) {
+    if (kMode == kStepFeedback) {  // full feedback, then a device-wide barrier
+      feedback_items(kp, ws, s, blockIdx.x * kWarps + threadIdx.y, gridDim.x * kWarps);
+      if (!grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go)) return;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
       atomicExch(&kp.bar->next[(s + 1) & 1], 0u);
     for (;;) {
@@ -974,7 +1027,7 @@ __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
       if ((long long)s >= ws.sc.remaining) continue;  // the scenario has finished
       if ((td.flags & kTfRing) || ws.b.is_child)
         strip_prepass(kp, ws, td, (int)((ws.sc.base + s) & 1));
-      if (kAnyTrack && ws.b.vmax) march_strip<T, kAnyTrack>(kp, ws, td, s);  // velocity tracked
+      if (kAnyTrack && ws.b.vmax) march_strip<T, true>(kp, ws, td, s);  // velocity tracked
       else march_strip<T, false>(kp, ws, td, s);
     }
     if (s + 1 < s_first + s_count &&

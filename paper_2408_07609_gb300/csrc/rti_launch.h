@@ -18,9 +18,9 @@ cudaError_t launch_snapshot(const KParams<T>& kp, int grid, cudaStream_t st);
 // child edge fluxes of parity p materialised into the flux arrays
 template <class T>
 cudaError_t launch_fill_edges(const KParams<T>& kp, int grid, int parity, cudaStream_t st);
-// largest co-resident grid of the persistent kernel (the variant with or without the
-// maximum-velocity update) on the current device
+// largest co-resident grid of the persistent kernel variant `mode` (kStep*) on the
+// current device
 template <class T>
-cudaError_t persistent_grid(int* grid, int tx, int ty, bool track);
+cudaError_t persistent_grid(int* grid, int tx, int ty, int mode);
 
 }  // namespace rti

@@ -62,6 +62,11 @@ struct Blk {
 #endif
 };
 
+// variants of the step kernel
+constexpr int kStepPlain = 0;     // no block keeps the maximum velocity
+constexpr int kStepTrack = 1;     // some block keeps it
+constexpr int kStepFeedback = 2;  // + the full-feedback phase (cooperative launch)
+
 // nesting options of a block (Blk::nest)
 constexpr int kNestFull = 1;   // fine-to-coarse feedback on every covered parent cell
 constexpr int kNestConst = 2;  // piecewise-constant coarse-to-fine edge flux
@@ -82,12 +87,21 @@ struct Tile {
   int blk, x0, y0, flags;
 };
 
+// One item of the full-feedback phase: parent cells (I0 .. I0 + 31, J) inside the
+// footprint of child `kid`, of parent block `blk` (block-table indices).
+struct FbItem {
+  int blk, kid, J, I0;
+};
+
 template <class T>
 struct KParams {
   const Blk<T>* blk;
   const int* kids;
   const Tile* tiles;
   const int* ntiles;   // device-resident tile count (patched between chunks)
+  const FbItem* fb;    // full-feedback items (null when no member uses full feedback)
+  const int* nfb;      // device-resident item count
+  int fb_any;          // the group has full-feedback items (host-known; selects the phase)
   ScenDev* scen;
   int* status;         // group status (barrier timeout)
   Bar* bar;
