@@ -24,7 +24,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path
 UNITS = {
     "rti_fp64.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "rti_fp32.cu": [],
-    "rti_host.cu": [],
+    "rti_host.cu": ["-Xcompiler", "-pthread"],
 }
 
 
@@ -68,7 +68,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
             if verbose and log:
                 sys.stderr.write(log)
     tmp = out + f".tmp{os.getpid()}"
-    r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"],
+    r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static",
+                        "-Xcompiler", "-pthread"],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

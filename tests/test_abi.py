@@ -71,6 +71,34 @@ def test_create_rejects_cfl_before_any_device_call(rti):
     assert e.value.code == -1
 
 
+def test_threaded_input_scan_finds_the_first_offending_block(rti):
+    """Inputs above 4 x 2^20 cells are scanned by several host threads in chunks. The
+    answer is still the serial one: a non-finite value in any chunk is INVALID_ARG, a
+    block whose deepest cell breaks Eq. 4 is CFL, and the first offending block in
+    order decides between the two. All of it before any device call."""
+    nx, ny = 2100, 2100  # 4.41 M cells, five chunks
+    big = [blk(nx=nx, ny=ny, dx=100.0)]
+    n = np.zeros((ny, nx), np.float32)
+    h = np.full((ny, nx), 10.0)
+    h[-1, -1] = 1000.0  # the deepest cell sits in the last chunk: dx/dt = 100 < 140
+    with pytest.raises(rti.RtiError) as e:
+        rti.Handle(big, [h], [n], dt=1.0)
+    assert e.value.code == -2
+    h[-1, -1] = 10.0
+    n[ny - 3, 5] = np.inf  # a non-finite Manning n in the last chunk
+    with pytest.raises(rti.RtiError) as e:
+        rti.Handle(big, [h], [n], dt=1.0)
+    assert e.value.code == -1
+    # two blocks: the first breaks Eq. 4, the second holds a NaN -> CFL (first decides)
+    two = [blk(nx=300, ny=300, dx=810.0), blk(level=2, parent=0, nx=270, ny=270, i0=100,
+                                                j0=100, dx=270.0)]
+    hb = [np.full((300, 300), 8000.0), np.full((270, 270), np.nan)]
+    nb = [np.zeros((300, 300), np.float32), np.zeros((270, 270), np.float32)]
+    with pytest.raises(rti.RtiError) as e:
+        rti.Handle(two, hb, nb, dt=3.0)
+    assert e.value.code == -2
+
+
 def test_error_strings(rti):
     L = rti.lib()
     for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
