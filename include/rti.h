@@ -144,6 +144,16 @@ int rti_set_state(rti_handle* h, int block, const double* eta, const double* M,
  * fine-to-coarse ring replacement. V(t) = V(0) - out[1] + out[2] + out[3]. */
 int rti_get_budget(rti_handle* h, int block, double out[4]);
 
+/* Volume budget of the whole domain (binary64), over the root blocks, whose cells hold
+ * the water of the regions their children refine as well (the fine-to-coarse feedback
+ * keeps them consistent): volume = sum of out[0], boundary_outflow = volume that left
+ * through the domain's edges (radiation faces), clip_volume = volume the dry clip
+ * added, feedback_volume = change from the fine-to-coarse feedback, so that
+ * volume(t) = volume(0) - boundary_outflow + clip_volume + feedback_volume. Any output
+ * may be NULL. Waits for enqueued work. */
+int rti_volume(rti_handle* h, double* volume, double* boundary_outflow, double* clip_volume,
+               double* feedback_volume);
+
 /* Host<->device bytes this handle's calls have copied so far (inputs, initial state,
  * outputs, checkpoints). */
 int rti_get_transfer_bytes(const rti_handle* h, long long* h2d, long long* d2h);

@@ -1220,6 +1220,24 @@ int rti_get_budget(rti_handle* h, int block, double out[4]) {
   return RTI_OK;
 }
 
+int rti_volume(rti_handle* h, double* volume, double* boundary_outflow, double* clip_volume,
+               double* feedback_volume) {
+  if (!h) return RTI_ERR_INVALID_ARG;
+  double acc[4] = {0, 0, 0, 0};
+  for (int k = 0; k < (int)h->blocks.size(); ++k) {
+    if (h->blocks[k].parent >= 0) continue;
+    double b[4];
+    const int rc = rti_get_budget(h, k, b);
+    if (rc) return rc;
+    for (int q = 0; q < 4; ++q) acc[q] += b[q];
+  }
+  if (volume) *volume = acc[0];
+  if (boundary_outflow) *boundary_outflow = acc[1];
+  if (clip_volume) *clip_volume = acc[2];
+  if (feedback_volume) *feedback_volume = acc[3];
+  return RTI_OK;
+}
+
 int rti_get_transfer_bytes(const rti_handle* h, long long* h2d, long long* d2h) {
   if (!h || !h2d || !d2h) return RTI_ERR_INVALID_ARG;
   *h2d = h->h2d;

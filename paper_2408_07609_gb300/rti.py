@@ -79,6 +79,7 @@ def lib():
             "rti_get_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
             "rti_set_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
             "rti_get_budget": (C.c_int, [_vp, C.c_int, _dp]),
+            "rti_volume": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
             "rti_get_transfer_bytes": (C.c_int, [_vp, C.POINTER(C.c_longlong),
                                                  C.POINTER(C.c_longlong)]),
             "rti_steps_done": (C.c_longlong, [_vp]),
@@ -242,6 +243,12 @@ class Handle:
         out = np.empty(4)
         self._chk(lib().rti_get_budget(self._h, k, out.ctypes.data_as(_dp)), "budget")
         return dict(volume=out[0], outflow=out[1], clip=out[2], ring=out[3])
+
+    def volume(self):
+        """Whole-domain budget over the root blocks (rti_volume)."""
+        v = [C.c_double(0.0) for _ in range(4)]
+        self._chk(lib().rti_volume(self._h, *[C.byref(x) for x in v]), "volume")
+        return dict(volume=v[0].value, outflow=v[1].value, clip=v[2].value, feedback=v[3].value)
 
     def transfer_bytes(self):
         a, b = C.c_longlong(0), C.c_longlong(0)

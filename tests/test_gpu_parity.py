@@ -296,3 +296,24 @@ def test_max_velocity_fp64_single_grid_and_nest(rti, oracle_mod):
     with pytest.raises(rti.RtiError) as e:
         h.max_velocity(0)
     assert e.value.code == -8
+
+
+def test_domain_volume_budget_closes(rti, oracle_mod):
+    """rti_volume: the root level's budget of the whole domain. It equals the oracle's
+    root budget and closes: V(t) = V(0) - boundary outflow + clip + feedback."""
+    sc = _small_nest([(1, 54, 54), (1, 45, 45)])
+    h = rti.Handle.from_scenario(sc, precision=rti.FP64)
+    v0 = h.volume()
+    assert v0["outflow"] == 0 and v0["clip"] == 0 and v0["feedback"] == 0
+    o = oracle_mod.from_scenario(sc)
+    h.step(200)
+    o.step(200)
+    v = h.volume()
+    ob = o.budget(0)
+    assert abs(v["volume"] - ob["volume"]) <= 1e-12 * abs(ob["volume"])
+    for key, okey in (("outflow", "outflow"), ("clip", "clip"), ("feedback", "ring")):
+        assert abs(v[key] - ob[okey]) <= 1e-9 * max(1.0, abs(ob[okey])), key
+    assert v["outflow"] != 0 and v["feedback"] != 0
+    assert abs(v["volume"] - (v0["volume"] - v["outflow"] + v["clip"] + v["feedback"])) \
+        <= 1e-12 * v0["volume"]
+    h.close()
