@@ -470,7 +470,10 @@ def run_ours(a):
                           "paper_context": "Kochi 47.2 M cells: 82 s on 32 H100 PCIe, "
                                            "< 2.5 min on 32 Sapphire Rapids CPUs"},
             "e2e": e2e,
-            "gpu_launches": 3 if a.schedule == 0 else a.steps + 2,
+            # per timed rti_step: k_set_scen, the step kernel(s), k_advance; one launch
+            # per step adds k_feedback before each step with full feedback
+            "gpu_launches": 3 if a.schedule == 0 else
+                            a.steps * (2 if a.nest_feedback == "full" else 1) + 2,
             "serving": srv,
             "fp32_accuracy": acc,
             "fp32_accuracy_c4": acc4,
