@@ -43,6 +43,10 @@ MUTANTS = [
     ("nesting: full feedback patch one child row off",
      "for (int y = 3 * J; y < 3 * J + 3; ++y) { /* inner",
      "for (int y = 3 * J + 1; y < 3 * J + 4 && y < c->ny; ++y) { /* inner"),
+    ("front: outflow limit of half a cell", "double cap = (m > 0 ? Dlo : Dhi) * dx / (4.0 * dt);",
+     "double cap = (m > 0 ? Dlo : Dhi) * dx / (2.0 * dt);"),
+    ("front: outflow limit on the downwind cell", "double cap = (m > 0 ? Dlo : Dhi) * dx / (4.0 * dt);",
+     "double cap = (m > 0 ? Dhi : Dlo) * dx / (4.0 * dt);"),
     ("outputs: strict arrival threshold", "e >= p->arrival_thr", "e > p->arrival_thr"),
     ("outputs: max tracked on dry cells", "if (b->h[c] + e > p->dry_eps && e > b->emax[c])",
      "if (e > b->emax[c])"),
@@ -63,6 +67,7 @@ BATTERY = [
     pins.test_max_velocity_of_uniform_flow_is_exact,
     pins.test_max_velocity_is_zero_at_rest_and_on_dry_land_and_grows_monotonically,
     pins.test_max_and_arrival_are_functions_of_history,
+    pins.test_outflow_limit_on_a_puddle,
     pins.test_nest_constant_field_ring_average,
     pins.test_nest_edge_flux_reproduces_linear_profile,
     pins.test_constant_flux_gives_each_fine_face_its_coarse_face,

@@ -631,3 +631,33 @@ def test_nested_pulse_vs_fine_grid_for_every_option(oracle_mod):
         assert e[(1, fl)][1] <= 1.1 * e[(1, fl)][0]
     outside = [v[2] for v in e.values()]
     assert max(outside) - min(outside) <= 1e-3 * max(outside)
+
+
+def test_outflow_limit_on_a_puddle(oracle_mod):
+    """The outflow limit of the wet/dry front (reading R4): a face carries at most a
+    quarter of its upwind cell's water per step. A 0.1 m puddle in one cell of flat land
+    (ground 1 m above the datum, no friction, dt/dx = 1 s/m, which Eq. 4 allows because
+    no cell is sea) sees the front flux g D^2 dt/dx = 0.0981 m^2/s on each of its four
+    faces, which the limit cuts to D dx / (4 dt) = 0.025: after one step the four faces
+    carry exactly that outward, and after the second mass update the puddle is empty
+    and each neighbour holds 0.025 m, with the volume unchanged and no clip."""
+    nx = ny = 5
+    blk, hh, nn = single(nx, ny, 1.0, -1.0)
+    o = oracle_mod.Oracle([blk], [hh], [nn], dt=1.0)
+    eta = np.full((ny, nx), 1.0)
+    eta[2, 2] = 1.1
+    o.set_state(0, eta=eta)
+    v0 = o.budget(0)["volume"]
+    o.step(1)
+    _, M, N = o.get_state(0)
+    q = 0.1 * 1.0 / (4.0 * 1.0)
+    assert np.isclose(M[2, 3], q, rtol=1e-14, atol=0) and np.isclose(M[2, 2], -q, rtol=1e-14, atol=0)
+    assert np.isclose(N[3, 2], q, rtol=1e-14, atol=0) and np.isclose(N[2, 2], -q, rtol=1e-14, atol=0)
+    o.step(1)
+    e = o.get_state(0)[0]
+    depth = e + hh
+    assert abs(depth[2, 2]) <= 1e-14
+    for (j, i) in ((2, 1), (2, 3), (1, 2), (3, 2)):
+        assert np.isclose(depth[j, i], q, rtol=1e-12, atol=0)
+    b = o.budget(0)
+    assert b["clip"] <= 1e-15 and abs(b["volume"] - v0) <= 1e-12 * v0
