@@ -317,3 +317,29 @@ def test_domain_volume_budget_closes(rti, oracle_mod):
     assert abs(v["volume"] - (v0["volume"] - v["outflow"] + v["clip"] + v["feedback"])) \
         <= 1e-12 * v0["volume"]
     h.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_outflow_limit_puddle_matches_oracle(rti, oracle_mod, precision):
+    """The front's outflow limit on a draining 0.1 m puddle over flat land (the oracle
+    pin's case): binary64 to 1e-12, binary32 to 1e-6 m, after the limited step and the
+    one that empties the puddle."""
+    nx = ny = 5
+    blk = dict(level=1, parent=-1, nx=nx, ny=ny, i0=0, j0=0, dx=1.0, bc=(0, 0, 0, 0))
+    hh = np.full((ny, nx), -1.0)
+    nn = np.zeros((ny, nx), np.float32)
+    eta = np.full((ny, nx), 1.0)
+    eta[2, 2] = 1.1
+    h = rti.Handle([blk], [hh], [nn], dt=1.0, precision=precision)
+    h.set_state(0, eta=eta)
+    o = oracle_mod.Oracle([blk], [hh], [nn], dt=1.0)
+    o.set_state(0, eta=eta)
+    for _ in range(2):
+        h.step(1)
+        o.step(1)
+        for a, b in zip(h.get_state(0), o.get_state(0)):
+            if precision == 0:
+                assert relerr(a, b) <= TOL64
+            else:
+                assert np.abs(a - b).max() <= 1e-6
+    h.close()
