@@ -40,6 +40,9 @@ MUTANTS = [
      "if (p->nest_feedback == -1) return 1;"),
     ("nesting: constant flux still interpolated", "if (sub == 1 || constant) return v[k];",
      "if (sub == 1) return v[k];"),
+    ("nesting: chained exchange (each level receives before its parent packs)",
+     "    if (buf[k]) unpack_child(s, k, buf[k]);",
+     "    if (buf[k]) { pack_child(s, k, buf[k]); unpack_child(s, k, buf[k]); }"),
     ("nesting: full feedback patch one child row off",
      "for (int y = 3 * J; y < 3 * J + 3; ++y) { /* inner",
      "for (int y = 3 * J + 1; y < 3 * J + 4 && y < c->ny; ++y) { /* inner"),
@@ -72,6 +75,7 @@ BATTERY = [
     pins.test_nest_edge_flux_reproduces_linear_profile,
     pins.test_constant_flux_gives_each_fine_face_its_coarse_face,
     pins.test_full_feedback_sets_every_covered_cell_to_the_child_mean,
+    pins.test_full_feedback_exchange_is_simultaneous,
     pins.test_mirror_and_transpose_symmetry_bitwise,
     pins.test_friction_matches_manning_ode,
     pins.test_radiation_west_edge_absorbs,

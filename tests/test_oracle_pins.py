@@ -661,3 +661,41 @@ def test_outflow_limit_on_a_puddle(oracle_mod):
         assert np.isclose(depth[j, i], q, rtol=1e-12, atol=0)
     b = o.budget(0)
     assert b["clip"] <= 1e-15 and abs(b["volume"] - v0) <= 1e-12 * v0
+
+
+def test_full_feedback_exchange_is_simultaneous(oracle_mod):
+    """Full feedback with three levels: every level's means are formed before any level
+    receives, as in a pack-then-unpack exchange. So one step of the three-level nest
+    leaves the root exactly where the same step of the nest without the grandchild
+    leaves it (the root sees the child's own levels), while the grandchild, whose levels
+    differ from the child's, does change the child."""
+    dxp, h = 300.0, 10.0
+    P = dict(level=1, parent=-1, nx=90, ny=30, i0=0, j0=0, dx=dxp, bc=(1, 1, 0, 0))
+    Cb = dict(level=2, parent=0, nx=90, ny=54, i0=30, j0=6, dx=dxp / 3, bc=(0,) * 4)
+    G = dict(level=3, parent=1, nx=45, ny=36, i0=30, j0=20, dx=dxp / 9, bc=(0,) * 4)
+
+    def arrays(b):
+        return np.full((b["ny"], b["nx"]), h), np.zeros((b["ny"], b["nx"]), np.float32)
+
+    def pulse(b, x0, y0, amp, cx, cy):
+        x, y = np.meshgrid(x0 + centres(b["nx"], b["dx"]), y0 + centres(b["ny"], b["dx"]))
+        return amp * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * 2000.0 ** 2))
+
+    cx, cy = 45 * dxp, 15 * dxp
+    eP = pulse(P, 0.0, 0.0, 0.1, cx, cy)
+    eC = pulse(Cb, 30 * dxp, 6 * dxp, 0.1, cx, cy)
+    eG = pulse(G, 30 * dxp + 30 * dxp / 3, 6 * dxp + 20 * dxp / 3, 0.3, cx, cy)  # not the child's
+    runs = {}
+    for name, bl in (("three", [P, Cb, G]), ("two", [P, Cb])):
+        hs, ns = zip(*[arrays(b) for b in bl])
+        o = oracle_mod.Oracle(bl, list(hs), list(ns), dt=1.0, nest_feedback=oracle_mod.NEST_FULL)
+        o.set_state(0, eta=eP)
+        o.set_state(1, eta=eC)
+        if len(bl) == 3:
+            o.set_state(2, eta=eG)
+        o.step(1)
+        runs[name] = o
+    for a, b in zip(runs["three"].get_state(0), runs["two"].get_state(0)):
+        assert np.array_equal(a, b)
+    c3, c2 = runs["three"].get_state(1)[0], runs["two"].get_state(1)[0]
+    assert np.abs(c3 - c2).max() > 1e-3  # the grandchild's means reached the child
