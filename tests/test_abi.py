@@ -128,3 +128,17 @@ def test_velocity_tracking_adds_a_plane_and_is_refused_without_state(rti):
     with pytest.raises(rti.RtiError) as e:
         rti.step_noalloc(blk(nx=64, ny=64), rti.make_params(1.0, track_velocity=True), st, 0, 1)
     assert e.value.code == -1 and "track_velocity" in str(e.value)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No fallback: with the library absent, the first call raises (in a fresh process,
+    so the library this session loaded stays loaded)."""
+    import subprocess
+    import sys
+
+    code = ("from paper_2408_07609_gb300 import rti\n"
+            "try:\n    rti.lib()\nexcept RuntimeError as e:\n    print('raised', 'missing' in str(e))\n")
+    env = dict(os.environ, RTI_LIBRARY=str(tmp_path / "absent.so"), PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=120)
+    assert out.stdout.strip() == "raised True", out.stdout + out.stderr
