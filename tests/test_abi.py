@@ -142,3 +142,17 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                          timeout=120)
     assert out.stdout.strip() == "raised True", out.stdout + out.stderr
+
+
+def test_header_is_plain_c():
+    """include/rti.h compiles as C99 on its own: plain pointers and sizes, no C++ or
+    torch types in the boundary."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    r = subprocess.run([gcc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Werror",
+                        os.path.join(ROOT, "include", "rti.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
