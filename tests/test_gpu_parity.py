@@ -343,3 +343,19 @@ def test_outflow_limit_puddle_matches_oracle(rti, oracle_mod, precision):
             else:
                 assert np.abs(a - b).max() <= 1e-6
     h.close()
+
+
+def test_full_size_five_level_fp32_two_steps(rti, oracle_mod):
+    """The benchmark's own configuration (binary32, persistent launch, 28 x 64 strips)
+    on the 46.65 M-cell hierarchy, two steps, every cell of every block against the
+    oracle: levels within 1e-4 m and fluxes within 1e-4 of the block's largest flux
+    (binary32 rounding of a 5 m, 7 km-deep wave)."""
+    sc = S.config4(steps=2)
+    h, o = run_pair(rti, oracle_mod, sc, 2, precision=rti.FP32)
+    for k in range(len(sc.blocks)):
+        ge, gM, gN = h.get_state(k)
+        oe, oM, oN = o.get_state(k)
+        assert np.abs(ge - oe).max() <= 1e-4, k
+        for a, b in ((gM, oM), (gN, oN)):
+            assert np.abs(a - b).max() <= 1e-4 * max(np.abs(b).max(), 1e-3), k
+    h.close()
