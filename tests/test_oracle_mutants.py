@@ -50,6 +50,10 @@ MUTANTS = [
      "double cap = (m > 0 ? Dlo : Dhi) * dx / (2.0 * dt);"),
     ("front: outflow limit on the downwind cell", "double cap = (m > 0 ? Dlo : Dhi) * dx / (4.0 * dt);",
      "double cap = (m > 0 ? Dhi : Dlo) * dx / (4.0 * dt);"),
+    ("initial: no floor at the ground", "      if (e < -h) e = -h;\n    } else {",
+     "    } else {"),
+    ("initial: uplift on land too", "    } else {\n      e = -h;\n    }",
+     "    } else {\n      e = dz ? dz[c] : -h;\n    }"),
     ("outputs: strict arrival threshold", "e >= p->arrival_thr", "e > p->arrival_thr"),
     ("outputs: max tracked on dry cells", "if (b->h[c] + e > p->dry_eps && e > b->emax[c])",
      "if (e > b->emax[c])"),
@@ -71,6 +75,7 @@ BATTERY = [
     pins.test_max_velocity_is_zero_at_rest_and_on_dry_land_and_grows_monotonically,
     pins.test_max_and_arrival_are_functions_of_history,
     pins.test_outflow_limit_on_a_puddle,
+    pins.test_initial_condition_r10,
     pins.test_nest_constant_field_ring_average,
     pins.test_nest_edge_flux_reproduces_linear_profile,
     pins.test_constant_flux_gives_each_fine_face_its_coarse_face,

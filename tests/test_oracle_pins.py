@@ -699,3 +699,24 @@ def test_full_feedback_exchange_is_simultaneous(oracle_mod):
         assert np.array_equal(a, b)
     c3, c2 = runs["three"].get_state(1)[0], runs["two"].get_state(1)[0]
     assert np.abs(c3 - c2).max() > 1e-3  # the grandchild's means reached the child
+
+
+def test_initial_condition_r10(oracle_mod):
+    """R10: eta0 = max(dz, -h) on sea cells and -h on land whatever dz is; fluxes zero;
+    the maximum and the arrival start from eta0 (a cell at or above the threshold has
+    arrived at t = 0, a dry cell has no maximum)."""
+    nx, ny = 6, 4
+    h = np.array([[5.0, 5.0, 1.0, 0.5, -1.0, -2.0]] * ny)
+    blk, _, nn = single(nx, ny, 100.0, 0.0)
+    o = oracle_mod.Oracle([blk], [h], [nn], dt=1.0)
+    dz = np.array([[0.02, -7.0, -1.0, 0.005, 3.0, -0.5]] * ny)
+    o.set_initial_uplift(0, dz)
+    e, M, N = o.get_state(0)
+    want = np.array([[0.02, -5.0, -1.0, 0.005, 1.0, 2.0]] * ny)
+    assert np.array_equal(e, want)
+    assert not M.any() and not N.any()
+    mh, at = o.max_height(0), o.arrival_time(0)
+    wet = h + want > 1e-3
+    assert np.array_equal(np.isnan(mh), ~wet)
+    assert np.array_equal(mh[wet], want[wet])
+    assert np.array_equal(at, np.where(wet & (want >= 0.01), 0.0, -1.0))
