@@ -54,6 +54,10 @@ MUTANTS = [
      "    } else {"),
     ("initial: uplift on land too", "    } else {\n      e = -h;\n    }",
      "    } else {\n      e = dz ? dz[c] : -h;\n    }"),
+    ("friction: the smoother neighbour (x)", "double nf = b->n[L] > b->n[R] ? b->n[L] : b->n[R];",
+     "double nf = b->n[L] < b->n[R] ? b->n[L] : b->n[R];"),
+    ("friction: the cell's own roughness (y)", "double nf = b->n[S] > b->n[Nc] ? b->n[S] : b->n[Nc];",
+     "double nf = b->n[S];"),
     ("outputs: strict arrival threshold", "e >= p->arrival_thr", "e > p->arrival_thr"),
     ("outputs: max tracked on dry cells", "if (b->h[c] + e > p->dry_eps && e > b->emax[c])",
      "if (e > b->emax[c])"),
@@ -83,6 +87,7 @@ BATTERY = [
     pins.test_full_feedback_exchange_is_simultaneous,
     pins.test_mirror_and_transpose_symmetry_bitwise,
     pins.test_friction_matches_manning_ode,
+    pins.test_friction_takes_the_rougher_neighbour,
     pins.test_radiation_west_edge_absorbs,
     functools.partial(pins.test_standing_wave_discrete_period, cfl=0.7),
     pins.test_budget_closes_with_drying_and_radiation,

@@ -720,3 +720,34 @@ def test_initial_condition_r10(oracle_mod):
     assert np.array_equal(np.isnan(mh), ~wet)
     assert np.array_equal(mh[wet], want[wet])
     assert np.array_equal(at, np.where(wet & (want >= 0.01), 0.0, -1.0))
+
+
+def test_friction_takes_the_rougher_neighbour(oracle_mod):
+    """R2 friction at a face between cells of different roughness uses n_f = max(nL, nR)
+    (the stated reading). Uniform flow M0 over a flat bottom with Manning n alternating
+    by column (x faces) and by row (y faces): away from the walls, one step gives
+    M1 = (1 - F) M0 / (1 + F) with F = (dt/2) g n_f^2 |M0| / D^(7/3) on every face, and
+    the face between a smooth and a rough cell decays like the rough one."""
+    nx, ny, hd, dt, dx = 16, 16, 10.0, 1.0, 100.0
+    n = np.where((np.arange(nx)[None, :] + np.arange(ny)[:, None]) % 2 == 0, 0.02, 0.05)
+    blk, hh, _ = single(nx, ny, dx, hd)
+    o = oracle_mod.Oracle([blk], [hh], [n.astype(np.float32)], dt=dt)
+    M0 = 1.0
+    M = np.full((ny, nx + 1), M0)
+    M[:, 0] = M[:, nx] = 0.0
+    Nf = np.full((ny + 1, nx), M0)
+    Nf[0, :] = Nf[ny, :] = 0.0
+    o.set_state(0, eta=np.zeros((ny, nx)), M=M, N=Nf)
+    o.step(1)
+    _, M1, N1 = o.get_state(0)
+    n32 = n.astype(np.float32).astype(np.float64)
+    for f in range(4, nx - 3):  # x faces clear of the walls' influence, rows clear too
+        for j in range(4, ny - 4):
+            nf = max(n32[j, f - 1], n32[j, f])
+            F = 0.5 * dt * G * nf * nf * math.sqrt(M0 * M0 + M0 * M0) / (hd * hd * np.cbrt(hd))
+            assert math.isclose(M1[j, f], (1 - F) * M0 / (1 + F), rel_tol=1e-13), (j, f)
+    for g in range(4, ny - 3):
+        for i in range(4, nx - 4):
+            nf = max(n32[g - 1, i], n32[g, i])
+            F = 0.5 * dt * G * nf * nf * math.sqrt(M0 * M0 + M0 * M0) / (hd * hd * np.cbrt(hd))
+            assert math.isclose(N1[g, i], (1 - F) * M0 / (1 + F), rel_tol=1e-13), (g, i)
