@@ -58,6 +58,10 @@ MUTANTS = [
      "double nf = b->n[L] < b->n[R] ? b->n[L] : b->n[R];"),
     ("friction: the cell's own roughness (y)", "double nf = b->n[S] > b->n[Nc] ? b->n[S] : b->n[Nc];",
      "double nf = b->n[S];"),
+    ("nesting: mean not floored at the parent's ground",
+     "      if (avg < -P->h[pc]) avg = -P->h[pc];\n", ""),
+    ("mass: pressure from the old level", "double eL = b->eta1[L], eR = b->eta1[R]",
+     "double eL = b->eta[L], eR = b->eta[R]"),
     ("outputs: strict arrival threshold", "e >= p->arrival_thr", "e > p->arrival_thr"),
     ("outputs: max tracked on dry cells", "if (b->h[c] + e > p->dry_eps && e > b->emax[c])",
      "if (e > b->emax[c])"),
