@@ -62,6 +62,11 @@ MUTANTS = [
      "      if (avg < -P->h[pc]) avg = -P->h[pc];\n", ""),
     ("mass: pressure from the old level", "double eL = b->eta1[L], eR = b->eta1[R]",
      "double eL = b->eta[L], eR = b->eta[R]"),
+    ("advection: faces of dry depth still used",
+     "return f >= 1 && f <= b->nx - 1 && j >= 0 && j <= b->ny - 1 && dep_x(b, f, j) > eps;",
+     "return f >= 1 && f <= b->nx - 1 && j >= 0 && j <= b->ny - 1;"),
+    ("radiation: also from a dry edge cell", "  if (!(h + e > p->dry_eps)) return 0.0;\n  return sign",
+     "  return sign"),
     ("outputs: strict arrival threshold", "e >= p->arrival_thr", "e > p->arrival_thr"),
     ("outputs: max tracked on dry cells", "if (b->h[c] + e > p->dry_eps && e > b->emax[c])",
      "if (e > b->emax[c])"),
@@ -93,6 +98,7 @@ BATTERY = [
     pins.test_friction_matches_manning_ode,
     pins.test_friction_takes_the_rougher_neighbour,
     pins.test_radiation_west_edge_absorbs,
+    pins.test_dry_basin_with_open_edges_stays_dry,
     functools.partial(pins.test_standing_wave_discrete_period, cfl=0.7),
     pins.test_budget_closes_with_drying_and_radiation,
     pins.test_nested_budget_closes,

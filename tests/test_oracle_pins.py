@@ -751,3 +751,21 @@ def test_friction_takes_the_rougher_neighbour(oracle_mod):
             nf = max(n32[g - 1, i], n32[g, i])
             F = 0.5 * dt * G * nf * nf * math.sqrt(M0 * M0 + M0 * M0) / (hd * hd * np.cbrt(hd))
             assert math.isclose(N1[g, i], (1 - F) * M0 / (1 + F), rel_tol=1e-13), (g, i)
+
+
+def test_dry_basin_with_open_edges_stays_dry(oracle_mod):
+    """R6 radiation needs a wet edge cell: an empty basin (every sea cell dry, eta = -h,
+    ground below sea level) with radiation on all four edges has no water to move, so
+    it stays empty, bitwise, with nothing crossing its edges."""
+    nx, ny = 12, 10
+    rng = np.random.default_rng(3)
+    h = rng.uniform(0.5, 8.0, (ny, nx))
+    h[3:5, 6:9] = -2.0  # some land too
+    blk, _, nn = single(nx, ny, 100.0, 0.0, n=0.03, bc=(1, 1, 1, 1))
+    o = oracle_mod.Oracle([blk], [h], [nn], dt=1.0)
+    o.set_state(0, eta=-h)
+    o.step(100)
+    e, M, N = o.get_state(0)
+    assert np.array_equal(e, -h)
+    assert not M.any() and not N.any()
+    assert o.budget(0)["outflow"] == 0.0
