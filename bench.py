@@ -39,8 +39,8 @@ BYTES_PER_CELL_STEP = {"f32": 5 * 4 + 4 + 3 * 4,   # 36
 # dram__bytes_write.sum of one single-step launch on the 7.95 M-cell 4-level hierarchy,
 # divided by its cells); scaled to a launch of the bench by cells x steps. Set to None
 # whenever the kernel changes until it is captured again.
-# cell-steps of FP64 oracle work the reference arm spreads over its W + K steps (about a
-# minute on one host core)
+# cell-steps of FP64 oracle work per host thread the reference arm spreads over its W + K
+# steps (about a minute)
 REF_CELL_STEPS = 0.8e9
 NCU_F32_DRAM_BYTES_PER_CELL_STEP = (229.652992e6 + 83.252480e6) / 7.95e6  # 39.4 B
 
@@ -70,9 +70,16 @@ def parse():
     ap.add_argument("--serve-pool-gb", type=int, default=32)
     ap.add_argument("--serve-audit-every", type=int, default=10,
                     help="run every N-th request again in FP64 after the trace (0: no audit)")
+    ap.add_argument("--serve-sat-n", type=int, default=12,
+                    help="requests of the saturation comparison (all arrive at t = 0)")
+    ap.add_argument("--serve-sat-scale", type=float, default=1.0 / 120.0,
+                    help="duration scale of the saturation comparison")
+    ap.add_argument("--serve-real", action="store_true",
+                    help="also serve the 10-arrival smoke trace at its real durations (1-6 h)")
     ap.add_argument("--no-accuracy", action="store_true")
-    ap.add_argument("--accuracy-c4-steps", type=int, default=0,
-                    help="also compare FP32 with FP64 on the 46.65 M-cell workload over N steps")
+    ap.add_argument("--accuracy-c4-steps", type=int, default=2000,
+                    help="compare FP32 with FP64 on the 46.65 M-cell workload over N steps "
+                         "(0: skip)")
     ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
@@ -263,10 +270,14 @@ def time_e2e(rti, sc, steps, world):
 
 
 def serving(rti, sc5, a, world):
-    """Continuous-batching FP32 serving of a Poisson trace (mean inter-arrival 20 s, kinds
-    3-/4-/5-level uniform, 1-6 simulated hours), time-scaled by --serve-scale, beside the
-    plain per-scenario FP64 path (one request at a time, no batching) timed on a sample of
-    the same requests and applied to the trace's work."""
+    """Serving (C5). (1) A Poisson trace (mean inter-arrival 20 s, kinds 3-/4-/5-level
+    uniform, 1-6 simulated hours), arrivals and durations scaled by --serve-scale, through
+    the continuous-batching FP32 server: p50/p99 time to forecast, scenarios/h, the FP64
+    audit. (2) Capacity at saturation: the first --serve-sat-n requests of the trace all
+    arriving at t = 0 (durations scaled by --serve-sat-scale), served by the batched FP32
+    server and by the plain per-scenario FP64 path (each request created, stepped to its
+    end and read back alone, one after another), every request run in both. (3) With
+    --serve-real, the 10-arrival smoke trace at its real durations through the server."""
     import torch
 
     from paper_2408_07609_gb300 import scenarios as S
@@ -279,38 +290,42 @@ def serving(rti, sc5, a, world):
     srv = serve.Server(sites, pool_bytes=a.serve_pool_gb << 30, precision=rti.FP32,
                        chunk_steps=50, audit_every=a.serve_audit_every or None)
     reqs, st = srv.run(trace, time_scale=a.serve_scale, max_wall_s=180.0)
+    srv.audit_every = None
+    sat = [dict(t, arrival_s=0.0) for t in trace[:a.serve_sat_n]]
+    _, s32 = srv.run(sat, time_scale=a.serve_sat_scale, max_wall_s=300.0)
+    _, s64 = srv.run_plain(sat, precision=rti.FP64, time_scale=a.serve_sat_scale,
+                           max_wall_s=300.0)
+    real = None
+    if a.serve_real:
+        smoke = S.poisson_trace(seed=2025, n=10, mean_s=20.0)
+        _, real = srv.run(smoke, time_scale=1.0, max_wall_s=1800.0)
+        real = {k: real[k] for k in ("requests", "completed", "wall_s", "p50_s", "p99_s",
+                                     "mean_s", "scenarios_per_h", "max_live", "gcups",
+                                     "admit_s", "admit_max_s")}
+        real["trace"] = "10 Poisson arrivals (mean 20 s), 3/4/5-level uniform, 1-6 h, real durations"
     srv.close()
     del srv
     torch.cuda.empty_cache()
-    # plain FP64 path: each request alone, create .. results on host, one after another;
-    # timed on the smallest request of each kind, applied per kind to the trace's work
-    per_kind = {}
-    for r in sorted(reqs, key=lambda r: r.cells * r.nsteps):
-        if r.kind in per_kind:
-            continue
-        sc = S.with_new_source(sites[r.kind], r.seed)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h = rti.Handle.from_scenario(sc, precision=rti.FP64)
-        h.step(r.nsteps)
-        for k in range(len(sc.blocks)):
-            h.max_height(k)
-            h.arrival_time(k)
-        h.close()
-        per_kind[r.kind] = (time.perf_counter() - t0) / (r.cells * r.nsteps)
-    service64 = sum(r.cells * r.nsteps * per_kind[r.kind] for r in reqs)
+    keys = ("requests", "completed", "wall_s", "scenarios_per_h", "p50_s", "p99_s", "mean_s",
+            "max_live", "gcups")
     return {"scenarios_per_h": st["scenarios_per_h"], "p50_s": st["p50_s"], "p99_s": st["p99_s"],
             "mean_s": st["mean_s"], "completed": st["completed"], "requests": st["requests"],
             "max_live": st["max_live"], "gcups": st["gcups"], "precision": "fp32",
+            "admit_s": st["admit_s"], "admit_max_s": st["admit_max_s"],
             "fp64_audit": st["audit"],
             "trace": f"{a.serve_n} Poisson arrivals (mean 20 s), 3/4/5-level uniform, "
                      f"1-6 h; arrivals and durations x{a.serve_scale:.4g}; "
                      f"HBM pool {a.serve_pool_gb} GB; chunk 50 steps",
-            "fp64_plain": {"scenarios_per_h": len(reqs) / service64 * 3600.0,
-                           "gcups_by_kind": {k: 1e-9 / v for k, v in per_kind.items()},
-                           "how": "the smallest request of each kind alone in FP64 (create, "
-                                  "uplift, steps, results to host), one after another; its "
-                                  "time per cell-step applied to every request of that kind"}}
+            "saturation": {
+                "trace": f"the first {len(sat)} requests of the trace, all arriving at t = 0, "
+                         f"durations x{a.serve_sat_scale:.4g}; every request run by both arms",
+                "fp32_batched": {k: s32[k] for k in keys},
+                "fp64_plain": {k: s64[k] for k in keys},
+                "how": "fp32_batched: the continuous-batching server (one persistent launch "
+                       "per 50-step chunk over every live request, admission by footprint); "
+                       "fp64_plain: one request at a time in arrival order, created, stepped "
+                       "to its end and read back alone"},
+            "real_durations": real}
 
 
 def batch_c3(rti, steps=200, warmup=5):
@@ -359,7 +374,8 @@ def accuracy(rti, sc=None, steps=None):
     hs = {p: rti.Handle.from_scenario(sc, precision=p) for p in (rti.FP32, rti.FP64)}
     for h in hs.values():
         h.step(steps)
-    e_eta = e_max = 0.0
+    e_eta = e_max = e_open = 0.0
+    at_worst = None
     mis_wet = mis_ever = n = 0
     arr_err, arr_mis = [], 0
     for k, b in enumerate(sc.blocks):
@@ -367,7 +383,22 @@ def accuracy(rti, sc=None, steps=None):
         e32, e64 = hs[rti.FP32].get_state(k)[0], hs[rti.FP64].get_state(k)[0]
         m32, m64 = hs[rti.FP32].max_height(k), hs[rti.FP64].max_height(k)
         a32, a64 = hs[rti.FP32].arrival_time(k), hs[rti.FP64].arrival_time(k)
-        e_eta = max(e_eta, float(np.abs(e32 - e64).max()))
+        d = np.abs(e32 - e64)
+        if float(d.max()) > e_eta:
+            j, i = np.unravel_index(int(d.argmax()), d.shape)
+            at_worst = {"block": k, "cell": [int(i), int(j)], "depth64_m": float(h0[j, i] + e64[j, i]),
+                        "depth32_m": float(h0[j, i] + e32[j, i])}
+        e_eta = max(e_eta, float(d.max()))
+        # open water: the cell and its 8 neighbours wet in both runs (no front nearby)
+        wet = (h0 + e32 > sc.dry_eps) & (h0 + e64 > sc.dry_eps)
+        op = wet.copy()
+        op[1:, :] &= wet[:-1, :]
+        op[:-1, :] &= wet[1:, :]
+        op2 = op.copy()
+        op2[:, 1:] &= op[:, :-1]
+        op2[:, :-1] &= op[:, 1:]
+        if op2.any():
+            e_open = max(e_open, float(d[op2].max()))
         both = ~np.isnan(m32) & ~np.isnan(m64)
         if both.any():
             e_max = max(e_max, float(np.abs(m32[both] - m64[both]).max()))
@@ -381,7 +412,8 @@ def accuracy(rti, sc=None, steps=None):
         h.close()
     ae = np.concatenate(arr_err)
     return {"workload": sc.name, "against": "FP64 GPU path", "steps": steps,
-            "max_abs_eta_m": e_eta, "max_abs_max_height_m": e_max,
+            "max_abs_eta_m": e_eta, "max_abs_eta_open_water_m": e_open, "worst_cell": at_worst,
+            "max_abs_max_height_m": e_max,
             "wet_dry_mismatch_pct": 100.0 * mis_wet / n, "ever_wet_mismatch_pct": 100.0 * mis_ever / n,
             "arrival_max_err_s": float(ae.max()) if ae.size else 0.0,
             "arrival_mean_err_s": float(ae.mean()) if ae.size else 0.0,
@@ -390,17 +422,19 @@ def accuracy(rti, sc=None, steps=None):
             "arrival_mismatch_cells": arr_mis}
 
 
-def cpu_baseline(sc, steps):
-    """The FP64 oracle, as it stands, on the host: a bounded sample of the workload."""
+def cpu_baseline(sc, steps, parallel):
+    """The FP64 oracle, as it stands, on the host: a bounded sample of the workload, in
+    its OpenMP build over every host core (parallel) or single-threaded. Returns the
+    seconds of the steps and the threads used."""
     from oracle import oracle
 
     oracle.build()
-    o = oracle.from_scenario(sc)
+    o = oracle.from_scenario(sc, parallel=parallel)
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
     o.close()
-    return dt
+    return dt, (oracle.threads() if parallel else 1)
 
 
 def run_ours(a):
@@ -443,11 +477,15 @@ def run_ours(a):
     c3 = None if a.no_batch else batch_c3(rti)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        dt = cpu_baseline(sc, a.cpu_steps)
-        cpu = {"value": cells * a.cpu_steps / dt / 1e9, "unit": "GCUPS", "cores": 1,
+        dt, cores = cpu_baseline(sc, a.cpu_steps, parallel=True)
+        dt1, _ = cpu_baseline(sc, 1, parallel=False)
+        cpu = {"value": cells * a.cpu_steps / dt / 1e9, "unit": "GCUPS", "cores": cores,
                "kind": "oracle",
                "sample": f"{a.cpu_steps} FP64 steps of the full 46.65 M-cell hierarchy "
-                         "(single-threaded C oracle)"}
+                         f"(C oracle, OpenMP build, {cores} threads)",
+               "single_thread": {"value": cells / dt1 / 1e9, "unit": "GCUPS", "cores": 1,
+                                 "sample": "1 FP64 step of the full hierarchy, plain build"},
+               "nproc": os.cpu_count()}
     if rank == 0:
         emit({
             "metric": "GCUPS of the nested leap-frog step, 46.65 M-cell 5-level hierarchy, "
@@ -535,9 +573,10 @@ def run_reference(a):
     from oracle import oracle
 
     sc = workload()
-    sub, nblk, cells = reference_sample(sc, REF_CELL_STEPS / max(1, a.steps + a.warmup))
     oracle.build()
-    o = oracle.from_scenario(sub)
+    cores = oracle.threads()
+    sub, nblk, cells = reference_sample(sc, REF_CELL_STEPS * cores / max(1, a.steps + a.warmup))
+    o = oracle.from_scenario(sub, parallel=True)
     o.step(a.warmup)
     t0 = time.perf_counter()
     o.step(a.steps)
@@ -547,7 +586,7 @@ def run_reference(a):
     part = (f"first {nblk} of {len(sc.blocks)} blocks" if sub.blocks[0]["ny"] == sc.blocks[0]["ny"]
             else f"first {sub.blocks[0]['ny']} rows of the root block")
     sample = (f"{part} ({cells / 1e6:.2f} M of {sc.cells / 1e6:.2f} M cells) per step, "
-              "single-threaded C oracle")
+              f"C oracle, OpenMP build, {cores} threads")
     emit({"impl": "reference",
           "metric": "GCUPS of the nested leap-frog step, 46.65 M-cell 5-level hierarchy, "
                     "binary32 (binary64 and 6-h wall times beside it)",
@@ -555,7 +594,7 @@ def run_reference(a):
           "ms_per_step": dt / max(1, a.steps) * 1e3, "higher_is_better": True,
           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
           "config": {"workload": sc.name, "cells": sc.cells, "sample_cells": cells},
-          "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+          "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": cores, "kind": "oracle",
                            "sample": sample},
           "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 

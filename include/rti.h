@@ -37,7 +37,9 @@ extern "C" {
 #define RTI_ERR_NESTING -3     /* child not 1:3, not inside its parent with a 3-cell margin, overlapping siblings, parents not listed first */
 #define RTI_ERR_OOM -4         /* device memory exhausted or caller arena too small */
 #define RTI_ERR_NONFINITE -5   /* a non-finite water level appeared on the device */
-#define RTI_ERR_TIMEOUT -6     /* a device-wide barrier wait ran out; the state is undefined */
+#define RTI_ERR_TIMEOUT -6     /* a device-wide barrier wait ran out; the state is undefined until
+                                  rti_set_initial_uplift or rti_set_state sets it again (the
+                                  condition is cleared when it is reported) */
 #define RTI_ERR_CUDA -7        /* a CUDA runtime call failed (message in rti_last_error) */
 #define RTI_ERR_STATE -8       /* call not allowed in the current state (e.g. handle in a batch) */
 
@@ -194,8 +196,9 @@ const char* rti_error_string(int code);
  * eta0 on wet cells and -1e30 elsewhere; arrival_step at 0 where eta0 >= arrival_thr on
  * wet cells and -1 elsewhere. steps_done numbers the steps for the arrival record.
  *
- * The call steps nsteps times on `stream` (a cudaStream_t, NULL = legacy default), waits
- * for the work and returns its device status (RTI_ERR_NONFINITE, RTI_ERR_TIMEOUT). Its
+ * The call steps nsteps times on `stream` (a cudaStream_t, NULL = legacy default), reads
+ * the status words on that stream, synchronises the stream (it returns only when its
+ * work has finished) and returns the device status (RTI_ERR_NONFINITE, RTI_ERR_TIMEOUT). Its
  * first call on a device looks up the scratch address; make that first call before any
  * stream capture. Every call shares the one scratch array, which keeps the previous
  * call's contents (the call clears what must start at zero); calls that overlap on the

@@ -2,7 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY. Imported by the tests, by ``__graft_entry__.smoke()``
 and by the CPU-baseline leg of ``bench.py``; the product package never imports
-it. It builds the C source with gcc (no FMA contraction) into ``oracle/_build``.
+it. It builds the C source with gcc (no FMA contraction) into ``oracle/_build`` twice:
+single-threaded, and with OpenMP over the rows of each loop (``parallel=True``); the two
+builds give identical bits (the one in-step sum over cells is formed row by row in
+order in both).
 """
 from __future__ import annotations
 
@@ -15,6 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librti_oracle.so")
+LIB_OMP = os.path.join(BUILD, "librti_oracle_omp.so")
 SRC = os.path.join(HERE, "rti_oracle.c")
 
 BC_WALL, BC_RADIATION = 0, 1
@@ -22,18 +26,28 @@ ERRORS = {0: "ok", -1: "invalid argument", -2: "CFL violated", -3: "bad nesting"
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle. -ffp-contract=off: gcc fuses a*b+c on Arm by default."""
+    """Compile the oracle, single-threaded and with OpenMP. -ffp-contract=off: gcc fuses
+    a*b+c on Arm by default. Returns the single-threaded library's path."""
     os.makedirs(BUILD, exist_ok=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "rti_oracle.h"))
-    ):
-        tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-             "-shared", "-o", tmp, SRC, "-lm"]
-        )
-        os.replace(tmp, LIB)
+    src_t = max(os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "rti_oracle.h")))
+    for out, extra in ((LIB, []), (LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < src_t:
+            tmp = out + f".tmp{os.getpid()}"
+            subprocess.check_call(
+                ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                 *extra, "-shared", "-o", tmp, SRC, "-lm"]
+            )
+            os.replace(tmp, out)
     return LIB
+
+
+def threads() -> int:
+    """Threads the OpenMP build uses (OMP_NUM_THREADS, else every core this process may
+    run on)."""
+    v = os.environ.get("OMP_NUM_THREADS")
+    if v and v.isdigit():
+        return int(v)
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
 class _Block(C.Structure):
@@ -94,11 +108,15 @@ class Oracle:
 
     ``blocks`` is a list of dicts with keys level, parent, nx, ny, i0, j0, dx, bc
     (the same fields as the C-ABI block descriptor). ``bathy``/``manning`` are
-    lists of (ny, nx) arrays.
+    lists of (ny, nx) arrays. ``parallel=True`` runs the OpenMP build (same bits).
     """
 
     def __init__(self, blocks, bathy, manning, dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01,
-                 lib_path=None, nest_feedback=NEST_RING, nest_flux=FLUX_LINEAR):
+                 lib_path=None, nest_feedback=NEST_RING, nest_flux=FLUX_LINEAR,
+                 parallel=False):
+        if parallel and lib_path is None:
+            build()
+            lib_path = LIB_OMP
         self._L = L = lib(lib_path)
         nb = len(blocks)
         arr = (_Block * nb)()

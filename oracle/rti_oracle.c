@@ -6,6 +6,12 @@
  * no reordering beyond what the rules below state. Build with
  * -ffp-contract=off so that no multiply-add is fused.
  *
+ * The same source builds single-threaded and, with -fopenmp, with the rows of
+ * each loop shared among threads. Every cell's arithmetic is the same in both,
+ * and the one sum over cells inside a step (the clip volume of R5) is formed
+ * per row and then added row by row in order, so both builds give identical
+ * bits.
+ *
  * Source: Takahashi et al., "Modernizing an Operational Real-time Tsunami
  * Simulator to Support Diverse Hardware Platforms".
  *   Eq. 1 (Sec. II-A)  continuity  d(eta)/dt + dM/dx + dN/dy = 0
@@ -85,6 +91,7 @@ typedef struct {
   double* emax;
   long* arr;     /* arrival step, -1 if never */
   double* vmax2; /* R11: max squared cell-centre speed on wet instants (0 if never) */
+  double* rowsum; /* ny: the clip volume of each row in the current step */
   double outflow, clip, ring;
 } oblk;
 
@@ -102,7 +109,7 @@ struct orc_state {
 
 static void free_blk(oblk* b) {
   free(b->h); free(b->n); free(b->eta); free(b->eta1); free(b->M); free(b->M1);
-  free(b->N); free(b->N1); free(b->emax); free(b->arr); free(b->vmax2);
+  free(b->N); free(b->N1); free(b->emax); free(b->arr); free(b->vmax2); free(b->rowsum);
 }
 
 void orc_destroy(orc_state* s) {
@@ -186,8 +193,9 @@ orc_state* orc_create(const orc_block* blocks, int nblocks, const double* const*
     b->emax = (double*)malloc(nc * sizeof(double));
     b->arr = (long*)malloc(nc * sizeof(long));
     b->vmax2 = (double*)calloc(nc, sizeof(double));
+    b->rowsum = (double*)calloc((size_t)b->ny, sizeof(double));
     if (!b->h || !b->n || !b->eta || !b->eta1 || !b->M || !b->M1 || !b->N || !b->N1 ||
-        !b->emax || !b->arr || !b->vmax2)
+        !b->emax || !b->arr || !b->vmax2 || !b->rowsum)
       goto oom;
     for (size_t c = 0; c < nc; ++c) {
       b->h[c] = bathy[k][c];
@@ -224,6 +232,7 @@ static double speed2(const oblk* b, const double* eta, const double* M, const do
 
 /* R11 output update: the state a step starts from */
 static void track_speed(oblk* b, const orc_params* p) {
+#pragma omp parallel for schedule(static)
   for (int j = 0; j < b->ny; ++j)
     for (int i = 0; i < b->nx; ++i) {
       double s2 = speed2(b, b->eta, b->M, b->N, i, j, p);
@@ -266,19 +275,23 @@ int orc_set_initial_uplift(orc_state* s, int k, const double* dz) {
 /* ---- R1 + R5: mass (Eq. 1) over one block, with boundary outflow bookkeeping ---- */
 static void mass_block(oblk* b, const orc_params* p) {
   const double dtdx = b->dtdx, dx2 = b->dx * b->dx, vol = p->dt * b->dx;
+#pragma omp parallel for schedule(static)
   for (int j = 0; j < b->ny; ++j) {
+    double clip_row = 0.0;
     for (int i = 0; i < b->nx; ++i) {
       double Mw = b->M[FX(b, i, j)], Me = b->M[FX(b, i + 1, j)];
       double Ns = b->N[FY(b, i, j)], Nn = b->N[FY(b, i, j + 1)];
       size_t c = C(b, i, j);
       double e = b->eta[c] - (dtdx * (Me - Mw) + dtdx * (Nn - Ns));
       if (b->h[c] + e < 0) {
-        b->clip += (-b->h[c] - e) * dx2;
+        clip_row += (-b->h[c] - e) * dx2;
         e = -b->h[c];
       }
       b->eta1[c] = e;
     }
+    b->rowsum[j] = clip_row;
   }
+  for (int j = 0; j < b->ny; ++j) b->clip += b->rowsum[j];
   /* volume that left through the block's own boundary faces this step */
   for (int j = 0; j < b->ny; ++j) {
     b->outflow += vol * (-b->M[FX(b, 0, j)]);
@@ -303,6 +316,7 @@ static int receives(const orc_params* p, int I, int J, int a, int bb) {
 static void pack_child(const orc_state* s, int k, double* out) {
   const oblk* c = &s->b[k];
   int a = c->nx / 3, bb = c->ny / 3;
+#pragma omp parallel for schedule(static)
   for (int J = 0; J < bb; ++J) {
     for (int I = 0; I < a; ++I) {
       out[(size_t)J * a + I] = NAN;
@@ -513,8 +527,10 @@ static double radiate(const oblk* b, size_t c, double sign, const orc_params* p)
 /* ---- R2-R4 + R6: momentum (Eqs. 2-3) over one block ---- */
 static void momentum_block(oblk* b, const orc_params* p) {
   const int nx = b->nx, ny = b->ny;
+#pragma omp parallel for schedule(static)
   for (int j = 0; j < ny; ++j)
     for (int f = 1; f <= nx - 1; ++f) b->M1[FX(b, f, j)] = xmom(b, f, j, p);
+#pragma omp parallel for schedule(static)
   for (int g = 1; g <= ny - 1; ++g)
     for (int i = 0; i < nx; ++i) b->N1[FY(b, i, g)] = ymom(b, i, g, p);
   if (b->d.parent >= 0) { /* child edges are set by R7 after all blocks */
@@ -590,7 +606,9 @@ int orc_step(orc_state* s, int nsteps) {
     fine_to_coarse(s);
     for (int k = 0; k < s->nb; ++k) {
       oblk* b = &s->b[k];
-      for (size_t c = 0; c < (size_t)b->nx * b->ny; ++c) track_cell(b, c, step, &s->p);
+      const long nc = (long)b->nx * b->ny;
+#pragma omp parallel for schedule(static)
+      for (long c = 0; c < nc; ++c) track_cell(b, (size_t)c, step, &s->p);
     }
     for (int k = 0; k < s->nb; ++k) momentum_block(&s->b[k], &s->p);
     for (int k = 0; k < s->nb; ++k)

@@ -594,13 +594,22 @@ void advance_mirror(Group* g, int nsteps) {
   }
 }
 
+// The device status of a handle (and of the group that steps it). A barrier timeout is
+// reported once: the group's status word is cleared with the report, so that every later
+// launch of the group does not stop at its first barrier; the state stays undefined until
+// the caller sets a new one.
 int read_status(Group* g, rti_handle* h, std::string* err) {
   int st_h = 0, st_g = 0;
   cudaError_t e = cudaMemcpy(&st_h, h->arena + h->off_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && g) e = cudaMemcpy(&st_g, g->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_err(err, e, "status read");
-  if ((st_h | st_g) & kStTimeout)
-    return set_err(err, RTI_ERR_TIMEOUT, "device barrier wait timed out; state undefined");
+  if ((st_h | st_g) & kStTimeout) {
+    if (g) e = cudaMemset(g->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return cuda_err(err, e, "status reset");
+    return set_err(err, RTI_ERR_TIMEOUT,
+                   "device barrier wait timed out; state undefined until it is set again");
+  }
   if (st_h & kStNonFinite) return set_err(err, RTI_ERR_NONFINITE, "non-finite water level");
   return RTI_OK;
 }
@@ -1494,10 +1503,12 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
 #endif
     e = launch_chunk<T>(kp, p->schedule, grid, &s->counts[1], stream);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  // the two status words, read on the caller's stream behind the steps; the one wait
+  // below covers the steps and the copy
   int words[2] = {0, 0};
   if (e == cudaSuccess)
-    e = cudaMemcpy(words, &s->status_group, sizeof(words), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(words, &s->status_group, sizeof(words), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {
     t_create_err = std::string("rti_step_noalloc: ") + cudaGetErrorString(e);
     return RTI_ERR_CUDA;

@@ -11,8 +11,15 @@ Time to forecast is measured from a request's arrival to the moment its results 
 the host.
 
 The pool is one caller-owned device allocation (a torch uint8 tensor) carved first-fit
-into 256-byte aligned arenas, so admission and retirement allocate nothing on the
-device and never stall the running batch.
+into 256-byte aligned arenas, so admission and retirement allocate no arena of their
+own. Admissions happen between chunks: the host part of one (the request's source, the
+input scan of rti_create) runs while the chunk just launched is on the GPU, but
+rti_create and rti_set_initial_uplift synchronise the device, so the device part of an
+admission waits for that chunk and delays the next one. The server records the wall
+time spent admitting (admit_s) so that its share of the time to forecast is reported.
+
+`run_plain` serves the same trace the plain way for comparison: one request at a time
+in arrival order, each created, stepped to its end and read back alone.
 
 Audit: with audit_every = N, every N-th request (by arrival) is run again in binary64
 once the trace is served, off the forecast path, and its forecast outputs (maximum
@@ -83,6 +90,7 @@ class Request:
     footprint: int = 0
     cells: int = 0
     admitted_s: float = float("nan")
+    admit_wall_s: float = 0.0  # wall time of this request's admission (create + uplift)
     done_s: float = float("nan")
     result: dict = field(default_factory=dict)
     fields: dict = field(default_factory=dict)  # kept for the audit: block -> (max h, arrival)
@@ -180,18 +188,11 @@ class Server:
         requests join between two chunks (None: all that have arrived and fit). The
         binary64 audit of the sampled requests follows the trace.
         Returns (requests, stats)."""
-        reqs = []
-        for i, t in enumerate(trace):
-            site = self.sites[t["kind"]]
-            nsteps = max(1, int(round(t["hours"] * 3600.0 * time_scale / site.dt)))
-            r = Request(i, t["kind"], int(t["seed"]), float(t["hours"]),
-                        float(t["arrival_s"]) * time_scale, nsteps)
-            p = rti.make_params(site.dt, site.g, site.dry_eps, site.arrival_thr, self.prec)
-            r.footprint = rti.footprint(site.blocks, p)
-            r.cells = site.cells
+        reqs = self.requests(trace, time_scale)
+        for r in reqs:
             if r.footprint > self.pool.size:
-                raise ValueError(f"request {i} ({r.kind}) needs {r.footprint} B, pool is {self.pool.size}")
-            reqs.append(r)
+                raise ValueError(f"request {r.rid} ({r.kind}) needs {r.footprint} B, "
+                                 f"pool is {self.pool.size}")
         pending = list(reqs)
         live = {}
         max_live, chunks = 0, 0
@@ -212,9 +213,11 @@ class Server:
                 if admit_per_chunk is not None and admitted >= admit_per_chunk:
                     break
                 r = pending[0]
+                ta0 = time.perf_counter()
                 if not self._admit(r, live):
                     break
                 r.admitted_s = time.perf_counter() - t0
+                r.admit_wall_s = r.admitted_s - (ta0 - t0)
                 pending.pop(0)
                 admitted += 1
             max_live = max(max_live, len(live))
@@ -244,7 +247,67 @@ class Server:
                      p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
                      mean_s=float(lat.mean()), max_live=max_live, chunks=chunks,
                      gcups=cell_steps / wall / 1e9 if wall > 0 else float("nan"),
+                     admit_s=float(sum(r.admit_wall_s for r in reqs)),
+                     admit_max_s=float(max((r.admit_wall_s for r in reqs), default=0.0)),
                      time_scale=time_scale, audit=audit)
+        return reqs, stats
+
+    def requests(self, trace, time_scale: float = 1.0, precision=None):
+        """Request records of a trace (steps, footprint, cells) without serving it."""
+        prec = self.prec if precision is None else precision
+        out = []
+        for i, t in enumerate(trace):
+            site = self.sites[t["kind"]]
+            nsteps = max(1, int(round(t["hours"] * 3600.0 * time_scale / site.dt)))
+            r = Request(i, t["kind"], int(t["seed"]), float(t["hours"]),
+                        float(t["arrival_s"]) * time_scale, nsteps)
+            p = rti.make_params(site.dt, site.g, site.dry_eps, site.arrival_thr, prec)
+            r.footprint = rti.footprint(site.blocks, p)
+            r.cells = site.cells
+            out.append(r)
+        return out
+
+    def run_plain(self, trace, precision=rti.FP64, time_scale: float = 1.0,
+                  max_wall_s: float | None = None):
+        """The plain per-scenario path on the same trace: one request at a time, in arrival
+        order, each created in the pool, stepped to its end in one rti_step call and read
+        back (maximum height and arrival time of every block) before the next one starts.
+        Returns (requests, stats) like run()."""
+        reqs = self.requests(trace, time_scale, precision)
+        t0 = time.perf_counter()
+        for r in reqs:
+            now = time.perf_counter() - t0
+            if max_wall_s is not None and now > max_wall_s:
+                break
+            if r.arrival_s > now:
+                time.sleep(r.arrival_s - now)
+            sc = S.with_new_source(self.sites[r.kind], r.seed)
+            off = self.pool.alloc(r.footprint)
+            if off is None:
+                raise MemoryError(f"request {r.rid} does not fit the pool")
+            r.admitted_s = time.perf_counter() - t0
+            h = rti.Handle.from_scenario(sc, precision=precision, device_mem=self.pool.view(off))
+            h.step(r.nsteps, self.stream)
+            out = {}
+            for k in range(len(h.blocks)):
+                mh, at = h.max_height(k), h.arrival_time(k)
+                wet = ~np.isnan(mh)
+                out[k] = (float(np.nanmax(mh)) if wet.any() else float("nan"),
+                          int((at >= 0).sum()))
+            r.result = out
+            r.done_s = time.perf_counter() - t0
+            h.close()
+            self.pool.release(off)
+        wall = time.perf_counter() - t0
+        done = [r for r in reqs if np.isfinite(r.done_s)]
+        lat = np.array([r.latency_s for r in done]) if done else np.array([float("nan")])
+        cell_steps = float(sum(r.cells * r.nsteps for r in done))
+        stats = dict(requests=len(reqs), completed=len(done), wall_s=wall,
+                     scenarios_per_h=len(done) / wall * 3600.0 if wall > 0 else float("nan"),
+                     p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+                     mean_s=float(lat.mean()), max_live=1,
+                     gcups=cell_steps / wall / 1e9 if wall > 0 else float("nan"),
+                     time_scale=time_scale)
         return reqs, stats
 
     def close(self):

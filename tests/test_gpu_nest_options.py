@@ -16,7 +16,7 @@ import pytest
 from paper_2408_07609_gb300 import scenarios as S
 
 sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
-from test_gpu_parity import compare_fp64, relerr  # noqa: E402
+from parity import compare_fp64, relerr  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 OPTIONS = [(1, 0), (0, 1), (1, 1)]  # (nest_feedback, nest_flux); (0, 0) is the default

@@ -5,40 +5,18 @@ kernels round like the oracle; only the library cbrt may differ by an ulp).
 Binary32 bar: the accuracy stated for the forecast outputs (max |d eta| in metres,
 wet/dry mismatch, arrival error); see test_fp32_accuracy_report.
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
 from paper_2408_07609_gb300 import scenarios as S
 
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+from parity import TOL64, compare_fp64, relerr  # noqa: E402
+
 pytestmark = pytest.mark.gpu
-TOL64 = 1e-12
-
-
-def relerr(a, b):
-    scale = np.abs(b).max()
-    return np.abs(a - b).max() / scale if scale > 0 else np.abs(a - b).max()
-
-
-def compare_fp64(h, o, nblocks, tol=TOL64, outputs=True):
-    for k in range(nblocks):
-        ge, gM, gN = h.get_state(k)
-        oe, oM, oN = o.get_state(k)
-        for name, a, b in (("eta", ge, oe), ("M", gM, oM), ("N", gN, oN)):
-            assert relerr(a, b) <= tol, (k, name, relerr(a, b))
-        if outputs:
-            gh, oh = h.max_height(k), o.max_height(k)
-            assert np.array_equal(np.isnan(gh), np.isnan(oh)), k
-            m = ~np.isnan(oh)
-            if m.any():
-                assert relerr(gh[m], oh[m]) <= tol
-            ga, oa = h.arrival_time(k), o.arrival_time(k)
-            # arrival is a threshold crossing: equal except where the level sits within
-            # rounding of the threshold at the crossing step
-            assert (ga != oa).mean() <= 1e-4, k
-        gb, ob = h.budget(k), o.budget(k)
-        assert abs(gb["volume"] - ob["volume"]) <= 1e-12 * abs(ob["volume"])
-        for key in ("outflow", "clip", "ring"):
-            assert abs(gb[key] - ob[key]) <= 1e-9 * max(1.0, abs(ob[key])), key
 
 
 def run_pair(rti, oracle_mod, sc, steps, precision=0, schedule=0, tile=(0, 0)):

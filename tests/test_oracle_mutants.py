@@ -62,6 +62,12 @@ MUTANTS = [
      "      if (avg < -P->h[pc]) avg = -P->h[pc];\n", ""),
     ("mass: pressure from the old level", "double eL = b->eta1[L], eR = b->eta1[R]",
      "double eL = b->eta[L], eR = b->eta[R]"),
+    ("advection: face depth from the old level (x)",
+     "return 0.5 * (b->h[L] + b->h[R]) + 0.5 * (b->eta1[L] + b->eta1[R]);",
+     "return 0.5 * (b->h[L] + b->h[R]) + 0.5 * (b->eta[L] + b->eta[R]);"),
+    ("advection: face depth from the old level (y)",
+     "return 0.5 * (b->h[S] + b->h[Nc]) + 0.5 * (b->eta1[S] + b->eta1[Nc]);",
+     "return 0.5 * (b->h[S] + b->h[Nc]) + 0.5 * (b->eta[S] + b->eta[Nc]);"),
     ("advection: faces of dry depth still used",
      "return f >= 1 && f <= b->nx - 1 && j >= 0 && j <= b->ny - 1 && dep_x(b, f, j) > eps;",
      "return f >= 1 && f <= b->nx - 1 && j >= 0 && j <= b->ny - 1;"),
@@ -88,6 +94,7 @@ BATTERY = [
     pins.test_max_velocity_is_zero_at_rest_and_on_dry_land_and_grows_monotonically,
     pins.test_max_and_arrival_are_functions_of_history,
     pins.test_outflow_limit_on_a_puddle,
+    pins.test_advective_depth_is_the_new_level,
     pins.test_initial_condition_r10,
     pins.test_nest_constant_field_ring_average,
     pins.test_nest_edge_flux_reproduces_linear_profile,

@@ -236,6 +236,79 @@ def test_friction_matches_manning_ode(oracle_mod):
     assert 1.6 < errs[0] / errs[1] < 2.4
 
 
+# ------------------------------------------------------- advection: time level of the depth
+def stretching_flow(oracle_mod, along_x, dt, steps, dx=100.0, h=10.0, a0=1e-3, b0=5.0, n=200):
+    """Uniform stretching flow over a flat, frictionless bed: the flux grows linearly
+    along the flow, q(s) = a s + b (s = f dx at face f), the depth D is uniform and falls
+    as dD/dt = -a, so the water surface stays flat and the pressure term of Eqs. 2-3
+    vanishes; only the advective term d(q^2/D)/ds acts. The walls disturb the flow only
+    within two faces per step of themselves (the stencil's reach). Returns the oracle's
+    (a, b, D) after `steps` steps, fitted on the undisturbed middle faces, with the
+    largest deviation from the linear profile."""
+    ny = 3
+    nx_, ny_ = (n, ny) if along_x else (ny, n)
+    blk, hh, nn = single(nx_, ny_, dx, h)
+    o = oracle_mod.Oracle([blk], [hh], [nn], dt=dt)
+    q = a0 * np.arange(n + 1) * dx + b0
+    q[0] = q[n] = 0.0  # walls
+    if along_x:
+        o.set_state(0, eta=np.zeros((ny, n)), M=np.tile(q, (ny, 1)), N=np.zeros((ny + 1, n)))
+    else:
+        o.set_state(0, eta=np.zeros((n, ny)), M=np.zeros((n, ny + 1)),
+                    N=np.tile(q[:, None], (1, ny)))
+    o.step(steps)
+    e, M, N = o.get_state(0)
+    if along_x:
+        qf, ec, across = M[1], e[1], N
+    else:
+        qf, ec, across = N[:, 1], e[:, 1], M
+    lo, hi = 2 * steps + 4, n - 2 * steps - 4
+    s = np.arange(lo, hi + 1) * dx
+    a, b = np.polyfit(s, qf[lo:hi + 1], 1)
+    dev = np.abs(qf[lo:hi + 1] - (a * s + b)).max()
+    D = h + ec[lo:hi]
+    assert not across.any()  # the flow stays one-dimensional
+    assert np.ptp(D) <= 1e-12 * h  # and the surface flat
+    return a, b, D.mean(), dev
+
+
+def test_advective_depth_is_the_new_level(oracle_mod):
+    """R2/R3: the advective fluxes M^2/D, M Nbar/D (N^2/D, N Mbar/D) divide by the face
+    depth of the new level eta^{n+1}, the level at t^{n+1/2} where the leap-frog
+    momentum update of Eqs. 2-3 is centred (Sec. II-A) and which its pressure term
+    already uses. On the stretching flow of `stretching_flow` (walls far away, q > 0 so
+    the upwind difference takes the lower face) one step is, in closed form, with
+    D' = D - dt a the new depth:
+        a' = a (1 - 2 dt a / D'),   b' = b - dt a (2 b - a dx) / D'
+    (the a dx term is the upwind difference's own diffusion), and the oracle must follow
+    it to rounding in both directions. A depth from the old level eta^n gives
+    a' = a (1 - 2 dt a / D) instead. As dt -> 0 the recursion tends to the exact
+    solution of Eqs. 1-2 for this flow, a / D^2 constant (D(t) = D0 / (1 + a0 t / D0)),
+    which the oracle approaches at first order."""
+    dx, h, a0, b0, dt, K = 100.0, 10.0, 1e-3, 5.0, 2.0, 20
+    a, b, D = a0, b0, h
+    for _ in range(K):
+        D1 = D - dt * a
+        a, b, D = a * (1 - 2 * dt * a / D1), b - dt * a * (2 * b - a * dx) / D1, D1
+    a_old, D_old = a0, h
+    for _ in range(K):  # the old-level reading, for scale
+        a_old, D_old = a_old * (1 - 2 * dt * a_old / D_old), D_old - dt * a_old
+    assert abs(a - a_old) > 1e-7 * a  # the two readings differ far above rounding
+    for along_x in (True, False):
+        ga, gb, gD, dev = stretching_flow(oracle_mod, along_x, dt, K, dx, h, a0, b0)
+        assert dev <= 1e-12 * b0
+        assert abs(ga - a) <= 1e-11 * a, (along_x, ga, a, a_old)
+        assert abs(gb - b) <= 1e-11 * b, (along_x, gb, b)
+        assert abs(gD - D) <= 1e-12 * h
+    # first order towards the exact solution of the PDE over t = 40 s
+    T, errs = 40.0, []
+    exact_a = a0 / (1 + a0 * T / h) ** 2
+    for dt in (2.0, 1.0):
+        ga = stretching_flow(oracle_mod, True, dt, int(round(T / dt)), dx, h, a0, b0)[0]
+        errs.append(abs(ga - exact_a) / exact_a)
+    assert errs[0] < 1e-3 and 1.8 < errs[0] / errs[1] < 2.2
+
+
 # ------------------------------------------------------------------------- radiation
 def test_radiation_west_edge_absorbs(oracle_mod):
     """A left-going linear long wave (M = -c eta) leaves through the radiation edge;
