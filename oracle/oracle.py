@@ -89,6 +89,8 @@ def lib(path=None):
                      "orc_get_arrival_time",
                      "orc_get_budget"):
             getattr(L, name).argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc_cube_root.argtypes = [C.c_double]
+        L.orc_cube_root.restype = C.c_double
         _libs[key] = L
     return _libs[key]
 
@@ -203,6 +205,11 @@ class Oracle:
         out = np.empty(4)
         self._chk(self._L.orc_get_budget(self._s, k, _dptr(out)))
         return dict(volume=out[0], outflow=out[1], clip=out[2], ring=out[3])
+
+
+def cube_root(x):
+    """The oracle's cube root (the friction term's D^(7/3)) of one number."""
+    return lib().orc_cube_root(float(x))
 
 
 def from_scenario(sc, **kw):

@@ -83,6 +83,8 @@ int orc_get_max_velocity(const orc_state* s, int block, double* out);
  * the block boundary, out[2] = cumulative volume added by the dry clip, out[3] = cumulative
  * volume changed by the fine-to-coarse replacement of parent cells (R8). */
 int orc_get_budget(const orc_state* s, int block, double* out);
+/* the cube root the friction term uses (a stated Newton iteration; see rti_oracle.c) */
+double orc_cube_root(double x);
 
 #ifdef __cplusplus
 }

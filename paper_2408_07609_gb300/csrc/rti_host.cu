@@ -1,6 +1,7 @@
 // rti_host.cu -- the C ABI (include/rti.h): hierarchy validation, the device arena of a
 // handle, the tile work list of a group of handles, chunk launches and CUDA graphs,
 // batches, and host<->device transfers. No arithmetic of the time step runs here.
+#include <cuda.h>  // CUtensorMap and its encoding enums (the encoder is fetched at run time)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,6 +42,66 @@ constexpr int kIoThreads = 256, kIoBlocks = 1216;
 constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at the maximum SM clock
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---- TMA tensor maps of the step kernel's input planes
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once (the library links no driver API)
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// The map of one pitched plane (pitch x rows elements of `es` bytes at `base`), loading
+// boxes of kRingW x rs elements, zero-filled outside the plane.
+bool encode_plane(TMap* out, const void* base, int pitch, long long rows, size_t es, int rs) {
+  static_assert(sizeof(TMap) == sizeof(CUtensorMap), "tensor map size");
+  std::memset(out, 0, sizeof(TMap));
+  if (!base) return true;  // a plane the block does not have: never loaded
+  EncodeTiledFn enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
+  const cuuint32_t box[2] = {(cuuint32_t)kRingW, (cuuint32_t)rs};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt =
+      es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return enc(reinterpret_cast<CUtensorMap*>(out), dt, 2, const_cast<void*>(base), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The kMaps maps of a block descriptor (its planes and pitch), in the order of kMap*.
+template <class T>
+bool encode_maps(const Blk<T>& b, TMap* out) {
+  const long long rows = rows_for(b.ny);
+  const int rs = StageGeom<T>::RS;
+  bool ok = true;
+  for (int q = 0; q < 2; ++q) {
+    ok = ok && encode_plane(out + kMapEta + q, b.eta[q], b.pitch, rows, sizeof(T), rs);
+    ok = ok && encode_plane(out + kMapM + q, b.M[q], b.pitch, rows, sizeof(T), rs);
+    ok = ok && encode_plane(out + kMapN + q, b.N[q], b.pitch, rows, sizeof(T), rs);
+  }
+  ok = ok && encode_plane(out + kMapH, b.h, b.pitch, rows, sizeof(T), rs);
+  ok = ok && encode_plane(out + kMapEmax, b.emax, b.pitch, rows, sizeof(T), rs);
+  ok = ok && encode_plane(out + kMapMan, b.man, b.pitch, rows, 4, rs);
+  ok = ok && encode_plane(out + kMapVmax, b.vmax, b.pitch, rows, sizeof(T), rs);
+  return ok;
+}
 
 struct BlkMem {
   size_t eta[2], M[2], N[2], h, emax, man, arr, budget;
@@ -178,6 +239,8 @@ struct Group {
   int* d_counts = nullptr;  // [0] = ntiles, [1] = nscen, [2] = full-feedback items
   FbItem* d_fb = nullptr;
   size_t cap_fb = 0;
+  TMap* d_tmaps = nullptr;  // kMaps tensor maps per block of the block table
+  size_t cap_tmaps = 0;
   int nfb = 0;
   ScenDev* d_scen = nullptr;
   size_t cap_scen = 0;
@@ -301,6 +364,7 @@ void free_group_dev(Group* g) {
   cudaFree(g->d_tiles);
   cudaFree(g->d_counts);
   cudaFree(g->d_fb);
+  cudaFree(g->d_tmaps);
   cudaFree(g->d_scen);
   cudaFree(g->d_status);
   cudaFree(g->d_bar);
@@ -312,6 +376,7 @@ void free_group_dev(Group* g) {
   g->d_tiles = nullptr;
   g->d_counts = nullptr;
   g->d_fb = nullptr;
+  g->d_tmaps = nullptr;
   g->d_scen = nullptr;
   g->d_status = nullptr;
   g->d_bar = nullptr;
@@ -468,7 +533,16 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   if (e == cudaSuccess)
     e = grow(&g->d_scen, &g->cap_scen, g->members.size() * sizeof(ScenDev) + 64, &moved);
   if (e == cudaSuccess) e = grow(&g->d_fb, &g->cap_fb, fb.size() * sizeof(FbItem) + 64, &moved);
+  if (e == cudaSuccess)
+    e = grow(&g->d_tmaps, &g->cap_tmaps, blks.size() * kMaps * sizeof(TMap) + 64, &moved);
   if (e != cudaSuccess) return cuda_err(err, e, "device tables");
+  // the input planes of every block as TMA tensor maps, addressed from its descriptor
+  std::vector<TMap> tmaps(blks.size() * kMaps);
+  for (size_t i = 0; i < blks.size(); ++i) {
+    if (!encode_maps(blks[i], &tmaps[i * kMaps]))
+      return set_err(err, RTI_ERR_CUDA, "tensor map encoding (cuTensorMapEncodeTiled)");
+    blks[i].tm = g->d_tmaps + i * kMaps;
+  }
   // the captured graph holds the old pointers, the other kernel variant, or launches
   // with or without the feedback phase
   if ((moved || track != g->track || fb.empty() != (g->nfb == 0)) && g->gexec) {
@@ -481,8 +555,9 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   const size_t nb_tiles = tiles.size() * sizeof(Tile);
   const size_t nb_scen = g->members.size() * sizeof(ScenDev);
   const size_t nb_fb = fb.size() * sizeof(FbItem);
+  const size_t nb_tm = tmaps.size() * sizeof(TMap);
   const size_t need = align256(nb_blk) + align256(nb_kids) + align256(nb_tiles) +
-                      align256(nb_scen) + align256(nb_fb) + 256;
+                      align256(nb_scen) + align256(nb_fb) + align256(nb_tm) + 256;
   // the previous upload must have left the staging buffer before it is rewritten
   e = cudaEventSynchronize(g->staged);
   if (e != cudaSuccess) return cuda_err(err, e, "staging wait");
@@ -513,6 +588,7 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   if (e == cudaSuccess) e = put(tiles.data(), nb_tiles, g->d_tiles);
   if (e == cudaSuccess) e = put(sc.data(), nb_scen, g->d_scen);
   if (e == cudaSuccess) e = put(fb.data(), nb_fb, g->d_fb);
+  if (e == cudaSuccess) e = put(tmaps.data(), nb_tm, g->d_tmaps);
   if (e == cudaSuccess) e = put(counts, sizeof(counts), g->d_counts);
   if (e == cudaSuccess) e = cudaEventRecord(g->staged, st);
   if (e != cudaSuccess) return cuda_err(err, e, "table upload");
@@ -1389,7 +1465,8 @@ namespace {
 constexpr int kNoAllocMaxTiles = 4096;  // e.g. 2048 x 2048 cells in 28 x 64 strips (2368)
 
 struct NoAllocScratch {
-  Blk<double> blk;  // holds a Blk<float> or a Blk<double>
+  TMap maps[kMaps];  // tensor maps of the caller's planes
+  Blk<double> blk;   // holds a Blk<float> or a Blk<double>
   int counts[2];    // tiles, scenarios
   int status_group;
   int status_grid;
@@ -1412,10 +1489,15 @@ void* g_noalloc_addr[256];  // device address of the scratch, per device ordinal
 
 // Writes the tile list, the descriptor and the counters, and clears the barrier, the
 // status words and the budget partials (the array keeps the previous call's contents).
+struct MapSet {
+  TMap m[kMaps];
+};
+
 template <class T>
-__global__ void k_noalloc_setup(NoAllocScratch* s, Blk<T> b, int tx, int ty, int tiles_x,
-                                int tiles_y, long long steps_done, long long nsteps) {
+__global__ void k_noalloc_setup(NoAllocScratch* s, Blk<T> b, MapSet maps, int tx, int ty,
+                                int tiles_x, int tiles_y, long long steps_done, long long nsteps) {
   const int nt = tiles_x * tiles_y;
+  if (threadIdx.x < kMaps) s->maps[threadIdx.x] = maps.m[threadIdx.x];
   for (int k = threadIdx.x; k < nt; k += blockDim.x) {
     Tile t;
     t.blk = 0;
@@ -1479,7 +1561,14 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
   b.lo = nullptr;
   b.hi = reinterpret_cast<const char*>(~0ull);
 #endif
-  k_noalloc_setup<T><<<1, 256, 0, stream>>>(s, b, tx, ty, tiles_x, tiles_y, steps_done, nsteps);
+  MapSet maps;  // encoded on the host from the caller's pointers; the setup kernel stores them
+  if (!encode_maps(b, maps.m)) {
+    t_create_err = "rti_step_noalloc: tensor map encoding (cuTensorMapEncodeTiled) failed";
+    return RTI_ERR_CUDA;
+  }
+  b.tm = s->maps;
+  k_noalloc_setup<T><<<1, 256, 0, stream>>>(s, b, maps, tx, ty, tiles_x, tiles_y, steps_done,
+                                            nsteps);
   cudaError_t e = cudaGetLastError();
   int grid = 0;
   if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty, kStepPlain);

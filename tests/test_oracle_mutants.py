@@ -21,7 +21,13 @@ MUTANTS = [
      "Df = 0.5 * (hL + hR);"),
     ("pressure: y uses the x stencil", "grad = eN - eS;", "grad = eN - eN;"),
     ("friction: n instead of n^2", "p->g * nf * nf *", "p->g * nf *"),
-    ("friction: D^(4/3) instead of D^(7/3)", "(Df * Df * cbrt(Df))", "(Df * cbrt(Df))"),
+    ("friction: D^(4/3) instead of D^(7/3)", "(Df * Df * orc_cube_root(Df))",
+     "(Df * orc_cube_root(Df))"),
+    ("friction: cube root with two Newton steps", "for (int k = 0; k < 3; ++k) {",
+     "for (int k = 0; k < 2; ++k) {"),
+    ("friction: cube root start not scaled by 2^(-r/3)",
+     "double s = r == 0 ? 1.0 : (r == 1 ? 0.7937005259840998 : 0.6299605249474366);",
+     "double s = 1.0;"),
     ("advection: downwind on the x term", "if (w > 0) return okm ? phi0 - phim : 0.0;",
      "if (w > 0) return okp ? phip - phi0 : 0.0;"),
     ("advection: Nbar from the wrong row",
@@ -89,6 +95,7 @@ MUTANTS = [
 # cheapest first; each takes the oracle module as its only argument
 BATTERY = [
     pins.test_cfl_and_nesting_rejected,
+    pins.test_cube_root_is_within_four_ulp,
     pins.test_max_velocity_averages_the_two_faces_of_a_cell,
     pins.test_max_velocity_of_uniform_flow_is_exact,
     pins.test_max_velocity_is_zero_at_rest_and_on_dry_land_and_grows_monotonically,
@@ -129,7 +136,7 @@ def test_pins_catch_planted_mistake(oracle_mod, tmp_path, name, old, new):
                            "-o", so, str(csrc), "-lm"])
     fake = types.SimpleNamespace(
         Oracle=functools.partial(oracle_mod.Oracle, lib_path=so),
-        OracleError=oracle_mod.OracleError,
+        OracleError=oracle_mod.OracleError, lib=functools.partial(oracle_mod.lib, so),
         from_scenario=functools.partial(oracle_mod.from_scenario, lib_path=so),
         SRC=oracle_mod.SRC, NEST_RING=oracle_mod.NEST_RING, NEST_FULL=oracle_mod.NEST_FULL,
         FLUX_LINEAR=oracle_mod.FLUX_LINEAR, FLUX_CONSTANT=oracle_mod.FLUX_CONSTANT)

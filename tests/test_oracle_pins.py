@@ -309,6 +309,27 @@ def test_advective_depth_is_the_new_level(oracle_mod):
     assert errs[0] < 1e-3 and 1.8 < errs[0] / errs[1] < 2.2
 
 
+# --------------------------------------------------------------- the friction term's D^(7/3)
+def test_cube_root_is_within_four_ulp(oracle_mod):
+    """Eq. 2's friction divides by D^(7/3) = D^2 cbrt(D). The oracle takes the cube root
+    by a stated Newton iteration (so that a binary64 implementation with the same
+    operations rounds identically); it must be within 4 ulp of the correctly rounded cube
+    root over the depths a model meets (1 mm to 100 km), exact on exact cubes, and
+    monotone."""
+    L = oracle_mod.lib()
+    rng = np.random.default_rng(11)
+    xs = np.exp(rng.uniform(np.log(1e-3), np.log(1e5), 50000))
+    xs = np.concatenate([xs, [1e-3, 0.5, 1.0, 2.0, 4.0, 7000.0, 1e5]])
+    got = np.array([L.orc_cube_root(float(x)) for x in xs])
+    ref = np.cbrt(xs)
+    assert (np.abs(got - ref) / np.spacing(ref)).max() <= 4.0
+    for k in (1, 2, 3, 5, 10, 17, 100):
+        assert L.orc_cube_root(float(k) ** 3) == float(k)
+    srt = np.sort(xs)
+    cr = np.array([L.orc_cube_root(float(x)) for x in srt])
+    assert np.all(np.diff(cr) >= 0)
+
+
 # ------------------------------------------------------------------------- radiation
 def test_radiation_west_edge_absorbs(oracle_mod):
     """A left-going linear long wave (M = -c eta) leaves through the radiation edge;
