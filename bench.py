@@ -81,6 +81,10 @@ def parse():
                     help="compare FP32 with FP64 on the 46.65 M-cell workload over N steps "
                          "(0: skip)")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default launch shape (28 x 64 strips, all CTAs that fit, "
+                         "persistent) instead of the autotuner's choice")
+    ap.add_argument("--tune-cache", default=None, help="JSON file caching the tuned shapes")
     return ap.parse_args()
 
 
@@ -204,12 +208,13 @@ def handle_options(a):
                 track_velocity=bool(a.track_velocity))
 
 
-def time_device(rti, sc, precision, steps, warmup, schedule, world, tile=(0, 0), opts=None):
+def time_device(rti, sc, precision, steps, warmup, schedule, world, tile=(0, 0), opts=None,
+                ctas_per_sm=0):
     """Kernel-only rate: inputs resident in HBM, CUDA events on the launching stream."""
     import torch
 
     h = rti.Handle.from_scenario(sc, precision=precision, schedule=schedule, tile=tuple(tile),
-                                 **(opts or {}))
+                                 ctas_per_sm=ctas_per_sm, **(opts or {}))
     stream = torch.cuda.Stream()
     h.step(warmup, stream)
     h.sync()
@@ -237,7 +242,7 @@ def pinned_like(a, torch):
     return out
 
 
-def time_e2e(rti, sc, steps, world):
+def time_e2e(rti, sc, steps, world, shape=None):
     """The same rate through the public API with host buffers in pinned memory: create
     (bathymetry and Manning n copied in), initial uplift, the steps, and the forecast
     outputs (max depth and arrival time of every block) copied back into the caller's
@@ -253,8 +258,10 @@ def time_e2e(rti, sc, steps, world):
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    shape = shape or {}
     h = rti.Handle(sc.blocks, bathy, man, sc.dt, sc.g, sc.dry_eps, sc.arrival_thr,
-                   precision=rti.FP32)
+                   precision=rti.FP32, schedule=shape.get("schedule", 0),
+                   tile=(0, shape.get("tile_y", 0)), ctas_per_sm=shape.get("ctas_per_sm", 0))
     for k, u in enumerate(dz):
         if u is not None:
             h.set_initial_uplift(k, u)
@@ -287,8 +294,16 @@ def serving(rti, sc5, a, world):
              "4level": S.serving_hierarchy("4level", seed=1001, hours=0.0), "5level": sc5}
     trace = S.poisson_trace(seed=2024, n=a.serve_n, mean_s=20.0)
     barrier(world)
+    shape = {"tile_y": 0, "ctas_per_sm": 0}
+    if not a.no_autotune:
+        from paper_2408_07609_gb300 import autotune
+
+        mix = [S.with_new_source(sites[k], 7 + i) for i, k in enumerate(sorted(sites))]
+        t = autotune.tune_batch(mix, precision=rti.FP32, chunk_steps=(50,), tile_y=(32, 64, 96),
+                                ctas=(0, 4), cache_path=a.tune_cache)
+        shape = {"tile_y": t["tile_y"], "ctas_per_sm": t["ctas_per_sm"]}
     srv = serve.Server(sites, pool_bytes=a.serve_pool_gb << 30, precision=rti.FP32,
-                       chunk_steps=50, audit_every=a.serve_audit_every or None)
+                       chunk_steps=50, audit_every=a.serve_audit_every or None, **shape)
     reqs, st = srv.run(trace, time_scale=a.serve_scale, max_wall_s=180.0)
     srv.audit_every = None
     sat = [dict(t, arrival_s=0.0) for t in trace[:a.serve_sat_n]]
@@ -312,6 +327,7 @@ def serving(rti, sc5, a, world):
             "mean_s": st["mean_s"], "completed": st["completed"], "requests": st["requests"],
             "max_live": st["max_live"], "gcups": st["gcups"], "precision": "fp32",
             "admit_s": st["admit_s"], "admit_max_s": st["admit_max_s"],
+            "launch_shape": shape,
             "fp64_audit": st["audit"],
             "trace": f"{a.serve_n} Poisson arrivals (mean 20 s), 3/4/5-level uniform, "
                      f"1-6 h; arrivals and durations x{a.serve_scale:.4g}; "
@@ -328,21 +344,30 @@ def serving(rti, sc5, a, world):
             "real_durations": real}
 
 
-def batch_c3(rti, steps=200, warmup=5):
+def batch_c3(rti, steps=200, warmup=5, tune=True, cache=None):
     """C3: the 64 single grids (sides 128-1024, ~15.9 M cells) stepped together by one
     batch (one persistent, graph-captured launch per chunk), CUDA events around the
-    steps, in FP32 and FP64."""
+    steps, in FP32 (the autotuner's strip height, CTA cap and chunk length, and the
+    default shape beside it) and FP64 (default shape)."""
     import torch
 
     from paper_2408_07609_gb300 import scenarios as S
 
     grids = S.config3(count=64, steps=steps + warmup)
     cells = sum(g.cells for g in grids)
-    out = {"workload": f"64 grids, {cells / 1e6:.2f} M cells, chunk {steps} steps"}
-    for name, prec, n in (("fp32", rti.FP32, steps), ("fp64", rti.FP64, max(10, steps // 10))):
-        hs = [rti.Handle.from_scenario(g, precision=prec) for g in grids]
+    out = {"workload": f"64 grids, {cells / 1e6:.2f} M cells"}
+    runs = [("fp32_default", rti.FP32, steps, 0, 0), ("fp64", rti.FP64, max(10, steps // 10), 0, 0)]
+    if tune:
+        from paper_2408_07609_gb300 import autotune
+
+        t = autotune.tune_batch(grids, precision=rti.FP32, chunk_steps=(50, 100, 200),
+                                tile_y=(32, 64, 96), ctas=(0, 4), cache_path=cache)
+        runs.insert(0, ("fp32", rti.FP32, t["chunk_steps"], t["tile_y"], t["ctas_per_sm"]))
+        out["tuned"] = {k: t[k] for k in ("tile_y", "ctas_per_sm", "chunk_steps")}
+    for name, prec, n, ty, cap in runs:
+        hs = [rti.Handle.from_scenario(g, precision=prec, tile=(0, ty)) for g in grids]
         stream = torch.cuda.Stream()
-        b = rti.Batch(prec, rti.SCHED_PERSISTENT, n)
+        b = rti.Batch(prec, rti.SCHED_PERSISTENT, n, tile_y=ty, ctas_per_sm=cap)
         for h in hs:
             b.add(h, n + n)
         b.step(stream)  # warm-up chunk (uploads the tile list, captures the graph)
@@ -353,7 +378,8 @@ def batch_c3(rti, steps=200, warmup=5):
         e1.record(stream)
         b.sync()
         ms = e0.elapsed_time(e1)
-        out[name] = {"value": cells * n / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": n}
+        out[name] = {"value": cells * n / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": n,
+                     "tile_y": ty or 64, "ctas_per_sm": cap}
         b.close()
         for h in hs:
             h.close()
@@ -447,9 +473,19 @@ def run_ours(a):
     sc = workload()
     cells = sc.cells
     fp32_bytes = rti.footprint(sc.blocks, rti.make_params(sc.dt, precision=rti.FP32))
+    shape = {"tile_y": a.tile[1], "ctas_per_sm": 0, "schedule": a.schedule}
+    tuned = None
+    if not a.no_autotune and not a.tile[0]:
+        from paper_2408_07609_gb300 import autotune
+
+        tuned = autotune.tune_handle(sc, precision=rti.FP32, steps=(10, 40),
+                                     cache_path=a.tune_cache, tile_y=(32, 48, 64, 96, 128),
+                                     ctas=(0, 4), schedules=(rti.SCHED_PERSISTENT,),
+                                     **handle_options(a))
+        shape = {k: tuned[k] for k in ("tile_y", "ctas_per_sm", "schedule")}
     with Clocks(local) as clk:
-        ms32 = time_device(rti, sc, rti.FP32, a.steps, a.warmup, a.schedule, world, a.tile,
-                           handle_options(a))
+        ms32 = time_device(rti, sc, rti.FP32, a.steps, a.warmup, shape["schedule"], world,
+                           (0, shape["tile_y"]), handle_options(a), shape["ctas_per_sm"])
     clocks = clk.summary()
     ms32 = max_over_ranks(ms32, world)
     ms64 = time_device(rti, sc, rti.FP64, a.fp64_steps, max(3, a.warmup // 2), a.schedule, world,
@@ -464,7 +500,7 @@ def run_ours(a):
     achieved = bpc * cells * a.steps / (ms32 / 1e3) / 1e9  # GB/s of one launch of K steps
     e2e = None
     if not a.no_e2e:
-        wall, h2d, d2h = time_e2e(rti, sc, a.steps, world)
+        wall, h2d, d2h = time_e2e(rti, sc, a.steps, world, shape)
         wall = max_over_ranks(wall, world)
         e2e = {"value": world * cells * a.steps / wall / 1e9, "unit": "GCUPS",
                "h2d_bytes_per_step": h2d // a.steps, "d2h_bytes_per_step": d2h // a.steps,
@@ -474,7 +510,7 @@ def run_ours(a):
     srv = None if a.no_serving else serving(rti, sc, a, world)
     acc = None if (a.no_accuracy or rank != 0) else accuracy(rti)
     acc4 = None if (not a.accuracy_c4_steps or rank != 0) else accuracy(rti, sc, a.accuracy_c4_steps)
-    c3 = None if a.no_batch else batch_c3(rti)
+    c3 = None if a.no_batch else batch_c3(rti, tune=not a.no_autotune, cache=a.tune_cache)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         dt, cores = cpu_baseline(sc, a.cpu_steps, parallel=True)
@@ -495,8 +531,10 @@ def run_ours(a):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": sc.name, "cells": cells, "blocks": len(sc.blocks),
                        "levels": 5, "dt_s": sc.dt, "precision": "fp32",
-                       "schedule": "persistent" if a.schedule == 0 else "one launch per step",
-                       "strip": list(a.tile) if a.tile[0] else [28, 64],
+                       "schedule": "persistent" if shape["schedule"] == 0 else "one launch per step",
+                       "strip": [28, shape["tile_y"] or 64],
+                       "ctas_per_sm": shape["ctas_per_sm"] or "all that fit",
+                       "launch_shape_by": "autotuner" if tuned else "default",
                        "nesting": f"{a.nest_feedback} feedback, {a.nest_flux} edge flux",
                        "max_velocity": bool(a.track_velocity),
                        "l2": f"working set {fp32_bytes / 1e9:.2f} GB (fp32) > 129 MB L2; no flush",
@@ -510,9 +548,14 @@ def run_ours(a):
             "e2e": e2e,
             # per timed rti_step: k_set_scen, the step kernel(s), k_advance; one launch
             # per step adds k_feedback before each step with full feedback
-            "gpu_launches": 3 if a.schedule == 0 else
+            "gpu_launches": 3 if shape["schedule"] == 0 else
                             a.steps * (2 if a.nest_feedback == "full" else 1) + 2,
             "serving": srv,
+            "autotune": None if not tuned else {
+                "choice": shape, "ms_per_step_short_run": tuned["ms_per_step"],
+                "cached": tuned["cached"], "cost_model": tuned["model"],
+                "trials": [{k: t[k] for k in ("tile_y", "ctas_per_sm", "schedule", "ms_per_step")}
+                           for t in tuned["trials"]]},
             "fp32_accuracy": acc,
             "fp32_accuracy_c4": acc4,
             "batch_c3": c3,

@@ -89,6 +89,9 @@ typedef struct {
                          read of it per cell-step); 0: off. Not for rti_step_noalloc. */
   int nest_feedback;  /* RTI_NEST_RING (0, the default) or RTI_NEST_FULL */
   int nest_flux;      /* RTI_FLUX_LINEAR (0, the default) or RTI_FLUX_CONSTANT */
+  int ctas_per_sm;    /* resident CTAs per SM of the step kernel's grid: 0 = as many as fit
+                         (the occupancy limit), else at most this many (a tuning knob; the
+                         results do not depend on it) */
 } rti_params;
 
 typedef struct rti_handle rti_handle;
@@ -224,6 +227,16 @@ int rti_step_noalloc(const rti_block* grid, const rti_params* params,
  * rti_batch_step (rti_step returns RTI_ERR_STATE). Adding or removing members patches
  * the device-resident tile list; the captured CUDA graph is reused. */
 int rti_batch_create(int precision, int schedule, int chunk_steps, rti_batch** out);
+/* The same with the strip height and CTA cap of the batch (members must be created with
+ * the same tile_y); rti_batch_create uses tile_y 64 and no cap. */
+typedef struct {
+  int precision;   /* RTI_FP64 or RTI_FP32 */
+  int schedule;    /* RTI_SCHED_* */
+  int chunk_steps; /* steps per rti_batch_step */
+  int tile_y;      /* strip height, a multiple of 8; 0 = 64 */
+  int ctas_per_sm; /* as in rti_params */
+} rti_batch_config;
+int rti_batch_create_ex(const rti_batch_config* cfg, rti_batch** out);
 /* add a member that will take `nsteps` more steps, then stop */
 int rti_batch_add(rti_batch* b, rti_handle* h, long long nsteps);
 int rti_batch_remove(rti_batch* b, rti_handle* h);

@@ -1,7 +1,6 @@
 // rti_host.cu -- the C ABI (include/rti.h): hierarchy validation, the device arena of a
 // handle, the tile work list of a group of handles, chunk launches and CUDA graphs,
 // batches, and host<->device transfers. No arithmetic of the time step runs here.
-#include <cuda.h>  // CUtensorMap and its encoding enums (the encoder is fetched at run time)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,66 +41,6 @@ constexpr int kIoThreads = 256, kIoBlocks = 1216;
 constexpr long long kSpinCycles = 4000000000LL;  // ~2 s at the maximum SM clock
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// ---- TMA tensor maps of the step kernel's input planes
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// cuTensorMapEncodeTiled from the driver, looked up once (the library links no driver API)
-EncodeTiledFn encoder() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(f);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
-// The map of one pitched plane (pitch x rows elements of `es` bytes at `base`), loading
-// boxes of kRingW x rs elements, zero-filled outside the plane.
-bool encode_plane(TMap* out, const void* base, int pitch, long long rows, size_t es, int rs) {
-  static_assert(sizeof(TMap) == sizeof(CUtensorMap), "tensor map size");
-  std::memset(out, 0, sizeof(TMap));
-  if (!base) return true;  // a plane the block does not have: never loaded
-  EncodeTiledFn enc = encoder();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
-  const cuuint32_t box[2] = {(cuuint32_t)kRingW, (cuuint32_t)rs};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUtensorMapDataType dt =
-      es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  return enc(reinterpret_cast<CUtensorMap*>(out), dt, 2, const_cast<void*>(base), dims, strides,
-             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// The kMaps maps of a block descriptor (its planes and pitch), in the order of kMap*.
-template <class T>
-bool encode_maps(const Blk<T>& b, TMap* out) {
-  const long long rows = rows_for(b.ny);
-  const int rs = StageGeom<T>::RS;
-  bool ok = true;
-  for (int q = 0; q < 2; ++q) {
-    ok = ok && encode_plane(out + kMapEta + q, b.eta[q], b.pitch, rows, sizeof(T), rs);
-    ok = ok && encode_plane(out + kMapM + q, b.M[q], b.pitch, rows, sizeof(T), rs);
-    ok = ok && encode_plane(out + kMapN + q, b.N[q], b.pitch, rows, sizeof(T), rs);
-  }
-  ok = ok && encode_plane(out + kMapH, b.h, b.pitch, rows, sizeof(T), rs);
-  ok = ok && encode_plane(out + kMapEmax, b.emax, b.pitch, rows, sizeof(T), rs);
-  ok = ok && encode_plane(out + kMapMan, b.man, b.pitch, rows, 4, rs);
-  ok = ok && encode_plane(out + kMapVmax, b.vmax, b.pitch, rows, sizeof(T), rs);
-  return ok;
-}
 
 struct BlkMem {
   size_t eta[2], M[2], N[2], h, emax, man, arr, budget;
@@ -167,6 +106,7 @@ int validate(const rti_block* bl, int nb, const rti_params* p, std::string* why)
       (p->precision != RTI_FP32 && p->precision != RTI_FP64) ||
       (p->schedule != RTI_SCHED_PERSISTENT && p->schedule != RTI_SCHED_PER_PASS) ||
       (p->tile_x != 0 && p->tile_x != kStripW) || p->tile_y < 0 || p->tile_y % 8 ||
+      p->ctas_per_sm < 0 ||
       (p->track_velocity != 0 && p->track_velocity != 1) ||
       (p->nest_feedback != RTI_NEST_RING && p->nest_feedback != RTI_NEST_FULL) ||
       (p->nest_flux != RTI_FLUX_LINEAR && p->nest_flux != RTI_FLUX_CONSTANT)) {
@@ -239,8 +179,6 @@ struct Group {
   int* d_counts = nullptr;  // [0] = ntiles, [1] = nscen, [2] = full-feedback items
   FbItem* d_fb = nullptr;
   size_t cap_fb = 0;
-  TMap* d_tmaps = nullptr;  // kMaps tensor maps per block of the block table
-  size_t cap_tmaps = 0;
   int nfb = 0;
   ScenDev* d_scen = nullptr;
   size_t cap_scen = 0;
@@ -364,7 +302,6 @@ void free_group_dev(Group* g) {
   cudaFree(g->d_tiles);
   cudaFree(g->d_counts);
   cudaFree(g->d_fb);
-  cudaFree(g->d_tmaps);
   cudaFree(g->d_scen);
   cudaFree(g->d_status);
   cudaFree(g->d_bar);
@@ -376,7 +313,6 @@ void free_group_dev(Group* g) {
   g->d_tiles = nullptr;
   g->d_counts = nullptr;
   g->d_fb = nullptr;
-  g->d_tmaps = nullptr;
   g->d_scen = nullptr;
   g->d_status = nullptr;
   g->d_bar = nullptr;
@@ -385,7 +321,8 @@ void free_group_dev(Group* g) {
   g->cap_stream = nullptr;
 }
 
-int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, std::string* err) {
+int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, int cap,
+               std::string* err) {
   g->prec = prec;
   g->sched = sched;
   g->tx = tx;
@@ -404,14 +341,14 @@ int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, std::st
     if (c > 0) g->spin_cycles = c;
   }
   if (e == cudaSuccess) {
-    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid, tx, ty, kStepPlain)
-                         : persistent_grid<double>(&g->grid, tx, ty, kStepPlain);
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid, tx, ty, kStepPlain, cap)
+                         : persistent_grid<double>(&g->grid, tx, ty, kStepPlain, cap);
   if (e == cudaSuccess)
-    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_track, tx, ty, kStepTrack)
-                         : persistent_grid<double>(&g->grid_track, tx, ty, kStepTrack);
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_track, tx, ty, kStepTrack, cap)
+                         : persistent_grid<double>(&g->grid_track, tx, ty, kStepTrack, cap);
   if (e == cudaSuccess)
-    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_fb, tx, ty, kStepFeedback)
-                         : persistent_grid<double>(&g->grid_fb, tx, ty, kStepFeedback);
+    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_fb, tx, ty, kStepFeedback, cap)
+                         : persistent_grid<double>(&g->grid_fb, tx, ty, kStepFeedback, cap);
   }
   if (e != cudaSuccess) return cuda_err(err, e, "group setup");
   return RTI_OK;
@@ -533,16 +470,7 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   if (e == cudaSuccess)
     e = grow(&g->d_scen, &g->cap_scen, g->members.size() * sizeof(ScenDev) + 64, &moved);
   if (e == cudaSuccess) e = grow(&g->d_fb, &g->cap_fb, fb.size() * sizeof(FbItem) + 64, &moved);
-  if (e == cudaSuccess)
-    e = grow(&g->d_tmaps, &g->cap_tmaps, blks.size() * kMaps * sizeof(TMap) + 64, &moved);
   if (e != cudaSuccess) return cuda_err(err, e, "device tables");
-  // the input planes of every block as TMA tensor maps, addressed from its descriptor
-  std::vector<TMap> tmaps(blks.size() * kMaps);
-  for (size_t i = 0; i < blks.size(); ++i) {
-    if (!encode_maps(blks[i], &tmaps[i * kMaps]))
-      return set_err(err, RTI_ERR_CUDA, "tensor map encoding (cuTensorMapEncodeTiled)");
-    blks[i].tm = g->d_tmaps + i * kMaps;
-  }
   // the captured graph holds the old pointers, the other kernel variant, or launches
   // with or without the feedback phase
   if ((moved || track != g->track || fb.empty() != (g->nfb == 0)) && g->gexec) {
@@ -555,9 +483,8 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   const size_t nb_tiles = tiles.size() * sizeof(Tile);
   const size_t nb_scen = g->members.size() * sizeof(ScenDev);
   const size_t nb_fb = fb.size() * sizeof(FbItem);
-  const size_t nb_tm = tmaps.size() * sizeof(TMap);
   const size_t need = align256(nb_blk) + align256(nb_kids) + align256(nb_tiles) +
-                      align256(nb_scen) + align256(nb_fb) + align256(nb_tm) + 256;
+                      align256(nb_scen) + align256(nb_fb) + 256;
   // the previous upload must have left the staging buffer before it is rewritten
   e = cudaEventSynchronize(g->staged);
   if (e != cudaSuccess) return cuda_err(err, e, "staging wait");
@@ -588,7 +515,6 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   if (e == cudaSuccess) e = put(tiles.data(), nb_tiles, g->d_tiles);
   if (e == cudaSuccess) e = put(sc.data(), nb_scen, g->d_scen);
   if (e == cudaSuccess) e = put(fb.data(), nb_fb, g->d_fb);
-  if (e == cudaSuccess) e = put(tmaps.data(), nb_tm, g->d_tmaps);
   if (e == cudaSuccess) e = put(counts, sizeof(counts), g->d_counts);
   if (e == cudaSuccess) e = cudaEventRecord(g->staged, st);
   if (e != cudaSuccess) return cuda_err(err, e, "table upload");
@@ -1085,7 +1011,8 @@ int rti_create(const rti_block* blocks, int nblocks, const double* const* bathy,
   }
   h->self = new (std::nothrow) Group();
   if (!h->self) return fail(RTI_ERR_OOM);
-  rc = group_init(h->self, h->prec, params->schedule, h->params.tile_x, h->params.tile_y, 1, &h->err);
+  rc = group_init(h->self, h->prec, params->schedule, h->params.tile_x, h->params.tile_y, 1,
+                  params->ctas_per_sm, &h->err);
   if (rc) return fail(rc);
   h->self->members.push_back(h);
   h->self->remaining.push_back(0);
@@ -1363,12 +1290,21 @@ void rti_destroy(rti_handle* h) {
 
 // ------------------------------------------------------------------------------ batches
 int rti_batch_create(int precision, int schedule, int chunk_steps, rti_batch** out) {
-  if (!out || chunk_steps <= 0 || (precision != RTI_FP32 && precision != RTI_FP64) ||
-      (schedule != RTI_SCHED_PERSISTENT && schedule != RTI_SCHED_PER_PASS))
+  const rti_batch_config cfg = {precision, schedule, chunk_steps, 0, 0};
+  return rti_batch_create_ex(&cfg, out);
+}
+
+int rti_batch_create_ex(const rti_batch_config* cfg, rti_batch** out) {
+  if (!out || !cfg || cfg->chunk_steps <= 0 ||
+      (cfg->precision != RTI_FP32 && cfg->precision != RTI_FP64) ||
+      (cfg->schedule != RTI_SCHED_PERSISTENT && cfg->schedule != RTI_SCHED_PER_PASS) ||
+      cfg->tile_y < 0 || cfg->tile_y % 8 || cfg->ctas_per_sm < 0)
     return RTI_ERR_INVALID_ARG;
   rti_batch* b = new (std::nothrow) rti_batch();
   if (!b) return RTI_ERR_OOM;
-  int rc = group_init(&b->g, precision, schedule, kDefaultTx, kDefaultTy, chunk_steps, &b->err);
+  int rc = group_init(&b->g, cfg->precision, cfg->schedule, kDefaultTx,
+                      cfg->tile_y ? cfg->tile_y : kDefaultTy, cfg->chunk_steps, cfg->ctas_per_sm,
+                      &b->err);
   if (rc == RTI_OK && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
     rc = RTI_ERR_CUDA;
   if (rc) {
@@ -1465,8 +1401,7 @@ namespace {
 constexpr int kNoAllocMaxTiles = 4096;  // e.g. 2048 x 2048 cells in 28 x 64 strips (2368)
 
 struct NoAllocScratch {
-  TMap maps[kMaps];  // tensor maps of the caller's planes
-  Blk<double> blk;   // holds a Blk<float> or a Blk<double>
+  Blk<double> blk;  // holds a Blk<float> or a Blk<double>
   int counts[2];    // tiles, scenarios
   int status_group;
   int status_grid;
@@ -1489,15 +1424,10 @@ void* g_noalloc_addr[256];  // device address of the scratch, per device ordinal
 
 // Writes the tile list, the descriptor and the counters, and clears the barrier, the
 // status words and the budget partials (the array keeps the previous call's contents).
-struct MapSet {
-  TMap m[kMaps];
-};
-
 template <class T>
-__global__ void k_noalloc_setup(NoAllocScratch* s, Blk<T> b, MapSet maps, int tx, int ty,
-                                int tiles_x, int tiles_y, long long steps_done, long long nsteps) {
+__global__ void k_noalloc_setup(NoAllocScratch* s, Blk<T> b, int tx, int ty, int tiles_x,
+                                int tiles_y, long long steps_done, long long nsteps) {
   const int nt = tiles_x * tiles_y;
-  if (threadIdx.x < kMaps) s->maps[threadIdx.x] = maps.m[threadIdx.x];
   for (int k = threadIdx.x; k < nt; k += blockDim.x) {
     Tile t;
     t.blk = 0;
@@ -1561,17 +1491,10 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
   b.lo = nullptr;
   b.hi = reinterpret_cast<const char*>(~0ull);
 #endif
-  MapSet maps;  // encoded on the host from the caller's pointers; the setup kernel stores them
-  if (!encode_maps(b, maps.m)) {
-    t_create_err = "rti_step_noalloc: tensor map encoding (cuTensorMapEncodeTiled) failed";
-    return RTI_ERR_CUDA;
-  }
-  b.tm = s->maps;
-  k_noalloc_setup<T><<<1, 256, 0, stream>>>(s, b, maps, tx, ty, tiles_x, tiles_y, steps_done,
-                                            nsteps);
+  k_noalloc_setup<T><<<1, 256, 0, stream>>>(s, b, tx, ty, tiles_x, tiles_y, steps_done, nsteps);
   cudaError_t e = cudaGetLastError();
   int grid = 0;
-  if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty, kStepPlain);
+  if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty, kStepPlain, p->ctas_per_sm);
   if (e == cudaSuccess) {
     KParams<T> kp;
     std::memset(&kp, 0, sizeof(kp));

@@ -5,7 +5,7 @@
 namespace rti {
 
 template <>
-cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty, int mode) {
+cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty, int mode, int cap) {
   (void)tx;
   (void)ty;
   int dev = 0, sms = 0, per = 0;
@@ -20,6 +20,7 @@ cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty, int mode) {
                                                             kWarps * 32, 0)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T, kStepPlain>,
                                                             kWarps * 32, 0);
+  if (e == cudaSuccess && cap > 0 && per > cap) per = cap;
   if (e == cudaSuccess) *grid = sms * (per > 0 ? per : 1);
   return e;
 }

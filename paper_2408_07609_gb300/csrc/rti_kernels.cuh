@@ -391,108 +391,118 @@ struct Raw {
   T vm;  // squared-speed maximum (velocity tracking only)
 };
 
-// The march's input rows are staged ahead in shared memory by the tensor memory
-// accelerator: a warp keeps NS stages, each holding RS consecutive rows of its kRingW
-// columns of every input array (eta^n, h, M^n, N^n of the face above, eta_max, Manning n,
-// and the speed maximum when it is tracked), one 2-D box per array. Lane 0 issues the
-// boxes of a stage (cp.async.bulk.tensor, completing on the stage's mbarrier); every lane
-// waits on the mbarrier before the stage's first row, and once all lanes have read a
-// stage's last row (a __syncwarp), lane 0 refills it with the stage NS further on. Boxes
-// that reach past the plane are filled with zeros by the copy engine, like the margins.
+// The march's input rows are staged ahead in shared memory: a ring of kRingD slots per
+// warp, each holding elements [x0 - 4, x0 + 32) of the six input rows of one row r.
+// 16-byte cp.async.cg copies (through L2, no registers held) keep kRingD - 2 rows per
+// warp in flight; a slot is refilled two rows after it was read, so one __syncwarp per
+// row orders the reads before the refill. A copy that would start past the allocated
+// row is a zero fill.
+// slots per warp, a power of two (slots are taken modulo by a mask): binary64 is bound by
+// its arithmetic and keeps fewer rows in flight, inside the 48 KB of static shared memory
 template <class T>
-struct Stage {
-  static constexpr int RS = StageGeom<T>::RS, NS = StageGeom<T>::NS;
-  static constexpr int kArr = (kRingW * RS * (int)sizeof(T) + 127) / 128 * 128;  // one box
-  static constexpr int kMan = (kRingW * RS * 4 + 127) / 128 * 128;
-  // byte offsets of the boxes in a stage (128-byte aligned, as the copies want)
-  static constexpr int oE = 0, oH = kArr, oM = 2 * kArr, oN = 3 * kArr, oEm = 4 * kArr,
-                       oNm = 5 * kArr, oVm = 5 * kArr + kMan;
-  static constexpr int kBytes = 6 * kArr + kMan;
-  // bytes one stage delivers: five state-precision boxes, Manning n, the speed maximum
-  static constexpr unsigned kTx = 5u * kRingW * RS * sizeof(T) + kRingW * RS * 4u;
-  static constexpr unsigned kTxTrack = kTx + kRingW * RS * sizeof(T);
-  static_assert(kBytes % 128 == 0, "stage size");
+struct RingD {
+  static constexpr int D = 8;
+};
+template <>
+struct RingD<double> {
+  static constexpr int D = 4;
+};
+constexpr int kRingW = 36;
+
+template <class T>
+struct __align__(16) RingSlot {
+  T e[kRingW], h[kRingW], m[kRingW], nn[kRingW], em[kRingW];
+  float nm[kRingW];
+  T vm[kRingW];  // squared-speed maximum, staged only when the block tracks it
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* mb, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// generic-proxy accesses to global and shared memory before async-proxy (TMA) accesses
-__device__ __forceinline__ void fence_proxy_async_all() {
-  asm volatile("fence.proxy.async;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned mb, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned mb, unsigned parity) {
-  unsigned ok;
+// One 16-byte copy, issued only where `issue` holds (a predicate on the instruction, not
+// a branch); `valid` false makes it a zero fill that reads nothing.
+__device__ __forceinline__ void cp_async16(bool issue, void* sdst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  const int n = valid ? 16 : 0;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(mb), "r"(parity)
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
+      "@p cp.async.cg.shared.global [%0], [%1], 16, %2;\n\t}" ::"r"(d),
+      "l"(gsrc), "r"(n), "r"((int)issue)
       : "memory");
-  return ok != 0;
 }
-// Wait for phase `parity` of an mbarrier, for at most `limit` clock cycles.
-static __device__ __noinline__ bool mbar_wait_slow(unsigned mb, unsigned parity, long long limit) {
-  const long long t0 = clock64();
-  while (!mbar_try(mb, parity))
-    if (clock64() - t0 > limit) return false;
-  return true;
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ bool mbar_wait(unsigned mb, unsigned parity, long long limit) {
-  return mbar_try(mb, parity) || mbar_wait_slow(mb, parity, limit);
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-// One 2-D box (columns x.., rows y..) of the plane `map` into shared memory at `dst`.
-__device__ __forceinline__ void tma_box(unsigned dst, const TMap* map, int x, int y, unsigned mb) {
+
+// Lanes issue the 16-byte chunks of row r (element `rowbase` = (r + 2) pitch + x0 is the
+// strip's column x0 - 4; N is taken one row up).
+// What a lane copies of every staged row (fixed for a strip): chunk k of the state
+// arrays and of Manning n, whether it has one, and whether it lies inside the row.
+struct StageLane {
+  int ke, km;
+  bool ie, oe, im, om;
+};
+template <class T>
+__device__ __forceinline__ StageLane stage_lane(int lane, int x0, int pitch) {
+  constexpr int E = 16 / (int)sizeof(T);  // elements per chunk
+  constexpr int NC = kRingW / E;          // chunks per row of a state array
+  constexpr int NM = kRingW / 4;          // chunks of Manning n (binary32)
+  static_assert(NC <= 32, "one chunk per lane");
+  StageLane L;
+  L.ie = lane < NC;
+  L.ke = (L.ie ? lane : NC - 1) * E;
+  L.oe = x0 + L.ke + E <= pitch;
+  L.im = lane < NM;
+  L.km = (L.im ? lane : NM - 1) * 4;
+  L.om = x0 + L.km + 4 <= pitch;
+  return L;
+}
+
+// The five state-array chunks of a lane under one predicate: shared destinations kRingW
+// elements (STRIDE bytes) apart from `d`.
+template <int STRIDE>
+__device__ __forceinline__ void cp_async16x5(bool issue, unsigned d, const void* g0,
+                                             const void* g1, const void* g2, const void* g3,
+                                             const void* g4, bool valid) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(map), "r"(x), "r"(y), "r"(mb)
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+      "@p cp.async.cg.shared.global [%0], [%1], 16, %7;\n\t"
+      "@p cp.async.cg.shared.global [%0+%8], [%2], 16, %7;\n\t"
+      "@p cp.async.cg.shared.global [%0+%9], [%3], 16, %7;\n\t"
+      "@p cp.async.cg.shared.global [%0+%10], [%4], 16, %7;\n\t"
+      "@p cp.async.cg.shared.global [%0+%11], [%5], 16, %7;\n\t}" ::"r"(d),
+      "l"(g0), "l"(g1), "l"(g2), "l"(g3), "l"(g4), "r"((int)issue), "r"(valid ? 16 : 0),
+      "n"(STRIDE), "n"(2 * STRIDE), "n"(3 * STRIDE), "n"(4 * STRIDE)
       : "memory");
 }
 
-// Lane 0: the boxes of one stage, rows y .. y + RS - 1 of the allocation (N one row up),
-// columns from element x; level p of the ping-pong arrays.
 template <class T, bool kTrack>
-__device__ __forceinline__ void issue_stage(unsigned char* st, unsigned long long* full,
-                                            const TMap* tm, int p, int x, int y) {
-  using G = Stage<T>;
-  const unsigned mb = smem_u32(full), d = smem_u32(st);
-  mbar_expect_tx(mb, kTrack ? G::kTxTrack : G::kTx);
-  tma_box(d + G::oE, tm + kMapEta + p, x, y, mb);
-  tma_box(d + G::oH, tm + kMapH, x, y, mb);
-  tma_box(d + G::oM, tm + kMapM + p, x, y, mb);
-  tma_box(d + G::oN, tm + kMapN + p, x, y + 1, mb);
-  tma_box(d + G::oEm, tm + kMapEmax, x, y, mb);
-  tma_box(d + G::oNm, tm + kMapMan, x, y, mb);
-  if (kTrack) tma_box(d + G::oVm, tm + kMapVmax, x, y, mb);
+__device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T* h, const T* M,
+                                          const T* N, const T* emax, const float* man,
+                                          const T* vmax, int rowbase, int pitch,
+                                          const StageLane& L, bool row_ok) {
+  static_assert(offsetof(RingSlot<T>, h) == kRingW * sizeof(T) &&
+                    offsetof(RingSlot<T>, em) == 4 * kRingW * sizeof(T),
+                "state rows kRingW elements apart");
+  const int g = L.oe ? rowbase + L.ke : rowbase;
+  cp_async16x5<kRingW * (int)sizeof(T)>(row_ok && L.ie,
+                                        (unsigned)__cvta_generic_to_shared(&S.e[L.ke]), eta + g,
+                                        h + g, M + g, N + g + pitch, emax + g, L.oe);
+  cp_async16(row_ok && L.im, &S.nm[L.km], man + (L.om ? rowbase + L.km : rowbase), L.om);
+  if (kTrack) cp_async16(row_ok && L.ie, &S.vm[L.ke], vmax + g, L.oe);
 }
 
 template <class T, bool kTrack>
-__device__ __forceinline__ Raw<T> read_row(const unsigned char* st, int rs, int lane) {
-  using G = Stage<T>;
-  const int k = rs * kRingW + lane + 2;
+__device__ __forceinline__ Raw<T> read_row(const RingSlot<T>& S, int lane) {
   Raw<T> R;
-  R.e = reinterpret_cast<const T*>(st + G::oE)[k];
-  R.h = reinterpret_cast<const T*>(st + G::oH)[k];
-  R.m = reinterpret_cast<const T*>(st + G::oM)[k];
-  R.nn = reinterpret_cast<const T*>(st + G::oN)[k];
-  R.em = reinterpret_cast<const T*>(st + G::oEm)[k];
-  R.nm = reinterpret_cast<const float*>(st + G::oNm)[k];
-  R.vm = kTrack ? reinterpret_cast<const T*>(st + G::oVm)[k] : T(0);
+  R.e = S.e[lane + 2];
+  R.h = S.h[lane + 2];
+  R.m = S.m[lane + 2];
+  R.nn = S.nn[lane + 2];
+  R.em = S.em[lane + 2];
+  R.nm = S.nm[lane + 2];
+  R.vm = kTrack ? S.vm[lane + 2] : T(0);
   return R;
 }
 
@@ -572,13 +582,11 @@ __device__ __forceinline__ T radiate_r(T h, T e, T sign, T eps, T g) {
   return sign * (dsqrt(g * (h > T(0) ? h : T(0))) * e);
 }
 
-// Per-warp shared memory: the input stages of the march and their mbarriers, the
-// strip's block descriptor (and its parent's), its scenario counters and the index of
-// the block staged.
+// Per-warp shared memory: the strip's block descriptor (and its parent's), its
+// scenario counters and the index of the block staged.
 template <class T>
 struct WarpSlot {
-  alignas(128) unsigned char stage[Stage<T>::NS][Stage<T>::kBytes];
-  unsigned long long full[Stage<T>::NS];  // mbarrier of each stage
+  RingSlot<T> ring[RingD<T>::D];
   Blk<T> b;
   Blk<T> P;
   ScenDev sc;
@@ -680,13 +688,10 @@ __device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<
 // Step strip td at chunk step s (one warp; ws holds the strip's staged descriptor, the
 // prepass has run). The budget slot of the strip receives sum(eta^{n+1}) and adds the
 // clip, outflow and ring terms.
-// `seq` counts the stages the warp has used so far (stage k of the strip takes slot
-// (seq + k) % NS, whose mbarrier then completes its phase (seq + k) / NS). Returns false
-// when a stage did not arrive within the wait limit (the status word says so).
 template <class T, bool kTrack>
-__device__ __forceinline__ bool march_strip(const KParams<T>& kp, WarpSlot<T>& ws, Tile td,
-                                            int s, unsigned& seq) {
-  using G = Stage<T>;
+__device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& ws, Tile td,
+                                            int s) {
+  constexpr int kRingD = RingD<T>::D;
   const int lane = threadIdx.x;
   const Blk<T>& b = ws.b;
   const ScenDev sc = ws.sc;
@@ -698,7 +703,11 @@ __device__ __forceinline__ bool march_strip(const KParams<T>& kp, WarpSlot<T>& w
   const T dtdx = b.dtdx, eps = b.eps, g = b.g;
   const MomK<T> K = mom_consts(b);
   const T thr = b.thr;
+  const T* etaP = b.eta[p];
+  const T* Mp = b.M[p];
   const T* Np = b.N[p];
+  const T* hh = b.h;
+  const float* man = b.man;
   T* etaQ = b.eta[q];
   T* Mq = b.M[q];
   T* Nq = b.N[q];
@@ -721,24 +730,17 @@ __device__ __forceinline__ bool march_strip(const KParams<T>& kp, WarpSlot<T>& w
   // element offsets within a plane fit in 32 bits (rti_create checks pitch x rows < 2^31)
   int o = (y0 - 2 + kYOff) * pitch + (c + kXOff);
 
-  // prologue: N^n of y-face (c, y0 - 2); the first NS stages of rows y0 - 2 .. ye
+  // prologue: N^n of y-face (c, y0 - 2); rows y0 - 2 .. y0 + kRingD - 5 staged
   T nS = col_ok ? __ldcg(Np + o) : T(0);  // y0 - 2 is below row 0 or an interior row
   T nSL = __shfl_up_sync(full, nS, 1);
-  const int x0 = td.x0;  // element x0 of a row is column x0 - 4, the first of a box
-  const int ybase = y0 - 2 + kYOff;
-  const int nst = (ye - (y0 - 2) + G::RS) / G::RS;
-  const TMap* tm = b.tm;
-  // Every lane orders its earlier accesses (this strip's prepass stores of child edge
-  // fluxes, the previous steps' stores seen through the barrier, the previous strip's
-  // reads of the stages) before the copy engine's reads and writes that follow.
-  fence_proxy_async_all();
-  __syncwarp();
-  if (lane == 0) {
-    for (int k = 0; k < G::NS && k < nst; ++k)
-      issue_stage<T, kTrack>(ws.stage[(seq + k) % G::NS], &ws.full[(seq + k) % G::NS], tm, p,
-                             x0, ybase + k * G::RS);
+  const int x0 = td.x0;
+  int rowbase = (y0 - 2 + kYOff) * pitch + x0;
+  const StageLane SL = stage_lane<T>(lane, x0, pitch);
+  for (int k = 0; k < kRingD - 2; ++k) {
+    stage_row<T, kTrack>(ws.ring[k], etaP, hh, Mp, Np, emax, man, vmax, rowbase + k * pitch,
+                         pitch, SL, y0 - 2 + k <= ye);
+    cp_async_commit();
   }
-  bool arrived = true;
   Row<T> A = {}, B = {}, C = {};
 
   // One row r from its inputs `cur`: X receives row r; Y, Z are rows r - 2, r - 1.
@@ -874,51 +876,40 @@ __device__ __forceinline__ bool march_strip(const KParams<T>& kp, WarpSlot<T>& w
     o += pitch;
   };
 
-  int k = 0, rs = 0;  // stage and row in it of row r
+  int slot = 0;  // ring slot of row r
   for (int r = y0 - 2; r <= ye; ++r) {
-    const unsigned sq = seq + (unsigned)k, sl_ = sq % G::NS;
-    if (rs == 0 && arrived) arrived = mbar_wait(smem_u32(&ws.full[sl_]), (sq / G::NS) & 1u,
-                                                kp.spin_cycles);
-    const Raw<T> cur = read_row<T, kTrack>(ws.stage[sl_], rs, lane);
+    // refill the slot of row r - 2: every lane read it before the __syncwarp of row r - 1
+    stage_row<T, kTrack>(ws.ring[(slot - 2) & (kRingD - 1)], etaP, hh, Mp, Np, emax, man,
+                         vmax, rowbase + (kRingD - 2) * pitch, pitch, SL,
+                         r + kRingD - 2 <= ye);
+    cp_async_commit();
+    cp_async_wait<kRingD - 2>();  // row r has landed
+    __syncwarp();                 // ... for every lane's chunks
+    const Raw<T> cur = read_row<T, kTrack>(ws.ring[slot], lane);
+    slot = (slot + 1) & (kRingD - 1);
+    rowbase += pitch;
     Row<T> X;
     row(cur, X, B, C, r);
     A = B;  // rows r-2, r-1, r
     B = C;
     C = X;
-    if (++rs == G::RS || r == ye) {  // every lane has read the stage: refill it
-      __syncwarp();
-      if (lane == 0 && k + G::NS < nst && arrived) {
-        fence_proxy_async();  // the reads above before the copy engine's writes
-        issue_stage<T, kTrack>(ws.stage[sl_], &ws.full[sl_], tm, p, x0, ybase + (k + G::NS) * G::RS);
-      }
-      rs = 0;
-      ++k;
-    }
   }
-  seq += (unsigned)nst;
-  if (!arrived) {  // a stage never arrived: report it, and wait (bounded) for what is in flight
-    if (lane == 0) atomicOr(kp.status, kStTimeout);
-    for (int j = 0; j < G::NS; ++j) {
-      const unsigned sq = seq - 1u - (unsigned)j;
-      mbar_wait(smem_u32(&ws.full[sq % G::NS]), (sq / G::NS) & 1u, kp.spin_cycles);
-    }
-    __syncwarp();
-    return false;
-  }
+
+  cp_async_wait<0>();  // (only empty groups can be outstanding here)
+  __syncwarp();
 
   // ---- the strip's budget partials (binary64, fixed reduction order)
   const double vs = warp_sum((double)vol_t);
   if (lane == 0 && !dfinite(vs)) atomicOr(b.status, kStNonFinite);
   const double cs = warp_sum((double)clip_t) * b.dx2, os = warp_sum((double)out_t) * b.vol,
-               rg = warp_sum((double)ring_t) * b.dx2;
+               rs = warp_sum((double)ring_t) * b.dx2;
   if (lane == 0) {
     double* slot = b.budget + 4 * (size_t)((y0 / kp.ty) * b.tiles_x + td.x0 / kp.tx);
     slot[0] = vs;
     slot[1] += cs;
     slot[2] += os;
-    slot[3] += rg;
+    slot[3] += rs;
   }
-  return true;
 }
 
 // ------------------------------------------------------------------ device-wide barrier
@@ -1041,17 +1032,11 @@ template <class T, int kMode>
 __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
     k_step(KParams<T> kp, int s_first, int s_count) {
   constexpr bool kAnyTrack = kMode != kStepPlain;
-  __shared__ __align__(128) WarpSlot<T> slots[kWarps];
+  __shared__ WarpSlot<T> slots[kWarps];
   __shared__ int go;
   WarpSlot<T>& ws = slots[threadIdx.y];
-  if (threadIdx.x == 0) {
-    ws.blk = -1;
-    for (int j = 0; j < Stage<T>::NS; ++j) mbar_init(&ws.full[j], 1);
-    fence_mbar_init();
-  }
+  if (threadIdx.x == 0) ws.blk = -1;
   __syncwarp();
-  unsigned seq = 0;      // stages this warp has used
-  bool stalled = false;  // a stage never arrived: no more strips in this launch
   unsigned gen = 0;
   if ((kMode == kStepFeedback || s_count > 1) && threadIdx.x == 0 && threadIdx.y == 0)
     gen = ld_acquire_u32(&kp.bar->gen);
@@ -1063,7 +1048,7 @@ __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
       atomicExch(&kp.bar->next[(s + 1) & 1], 0u);
-    while (!stalled) {
+    for (;;) {
       unsigned t = 0;
       if (threadIdx.x == 0) t = atomicAdd(&kp.bar->next[s & 1], 1u);
       t = __shfl_sync(0xffffffffu, t, 0);
@@ -1073,10 +1058,8 @@ __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
       if ((long long)s >= ws.sc.remaining) continue;  // the scenario has finished
       if ((td.flags & kTfRing) || ws.b.is_child)
         strip_prepass(kp, ws, td, (int)((ws.sc.base + s) & 1));
-      const bool ok = kAnyTrack && ws.b.vmax
-                          ? march_strip<T, true>(kp, ws, td, s, seq)  // velocity tracked
-                          : march_strip<T, false>(kp, ws, td, s, seq);
-      stalled = !ok;
+      if (kAnyTrack && ws.b.vmax) march_strip<T, true>(kp, ws, td, s);  // velocity tracked
+      else march_strip<T, false>(kp, ws, td, s);
     }
     if (s + 1 < s_first + s_count &&
         !grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go))

@@ -19,8 +19,8 @@ cudaError_t launch_snapshot(const KParams<T>& kp, int grid, cudaStream_t st);
 template <class T>
 cudaError_t launch_fill_edges(const KParams<T>& kp, int grid, int parity, cudaStream_t st);
 // largest co-resident grid of the persistent kernel variant `mode` (kStep*) on the
-// current device
+// current device, with at most `cap` CTAs per SM when cap > 0
 template <class T>
-cudaError_t persistent_grid(int* grid, int tx, int ty, int mode);
+cudaError_t persistent_grid(int* grid, int tx, int ty, int mode, int cap);
 
 }  // namespace rti

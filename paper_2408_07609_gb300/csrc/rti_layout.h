@@ -29,35 +29,6 @@ inline int pitch_for(int nx) {
 }
 inline long long rows_for(int ny) { return (long long)ny + 1 + 2 * kYOff; }
 
-// Staging of the step kernel's input rows: a strip's warp loads boxes of kRingW columns
-// (elements x0 .. x0 + 35 of a row, i.e. columns x0 - 4 .. x0 + 31 of the strip starting
-// at x0; a 16-byte multiple for both precisions) by RS rows, into NS stages in shared
-// memory, each stage one box of every input array.
-constexpr int kRingW = 36;
-template <class T>
-struct StageGeom {
-  static constexpr int RS = sizeof(T) == 4 ? 4 : 2;  // rows per stage
-  static constexpr int NS = 2;                        // stages per warp
-};
-
-// A TMA tensor map (CUtensorMap, 128 bytes, 64-byte aligned), encoded on the host; the
-// kernels only pass its address to cp.async.bulk.tensor.
-struct alignas(64) TMap {
-  unsigned long long w[16];
-};
-// The tensor maps of one block, in this order; each covers a whole pitched plane
-// (pitch x (ny + 5) elements) and loads boxes of kRingW columns x StageGeom<T>::RS rows.
-enum : int {
-  kMapEta = 0,   // eta[0], eta[1]
-  kMapM = 2,     // M[0], M[1]
-  kMapN = 4,     // N[0], N[1]
-  kMapH = 6,
-  kMapEmax = 7,
-  kMapMan = 8,   // binary32
-  kMapVmax = 9,  // encoded only when the block keeps the maximum velocity
-  kMaps = 10
-};
-
 // Per-block descriptor in device memory. T is the state precision.
 template <class T>
 struct Blk {
@@ -81,7 +52,6 @@ struct Blk {
   int nest;        // kNest* bits of the owning handle's nesting options
   double* budget;  // 4 doubles per tile of this block: sum(eta) snapshot, clip, outflow, ring
   int* status;     // the owning handle's device status word
-  const TMap* tm;  // the block's kMaps tensor maps (device memory)
   // constants in the state precision (all exactly the values the oracle uses in FP64)
   T dtdx, dt, g, cfric /* 0.5*dt*g */, eps, thr, dx, q4dt /* 4*dt */;
   // binary64 constants for the nesting sums and the budget

@@ -39,7 +39,12 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("g", C.c_double), ("dry_eps", C.c_double),
                 ("arrival_thr", C.c_double), ("precision", C.c_int), ("schedule", C.c_int),
                 ("tile_x", C.c_int), ("tile_y", C.c_int), ("track_velocity", C.c_int),
-                ("nest_feedback", C.c_int), ("nest_flux", C.c_int)]
+                ("nest_feedback", C.c_int), ("nest_flux", C.c_int), ("ctas_per_sm", C.c_int)]
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("precision", C.c_int), ("schedule", C.c_int), ("chunk_steps", C.c_int),
+                ("tile_y", C.c_int), ("ctas_per_sm", C.c_int)]
 
 
 class NoAllocState(C.Structure):
@@ -89,6 +94,7 @@ def lib():
             "rti_last_error": (C.c_char_p, [_vp]),
             "rti_error_string": (C.c_char_p, [C.c_int]),
             "rti_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_vp)]),
+            "rti_batch_create_ex": (C.c_int, [C.POINTER(BatchConfig), C.POINTER(_vp)]),
             "rti_batch_add": (C.c_int, [_vp, _vp, C.c_longlong]),
             "rti_batch_remove": (C.c_int, [_vp, _vp]),
             "rti_batch_step": (C.c_int, [_vp, _vp]),
@@ -128,11 +134,11 @@ def _blocks_array(blocks):
 
 def make_params(dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01, precision=FP64,
                 schedule=SCHED_PERSISTENT, tile=(0, 0), track_velocity=False,
-                nest_feedback=None, nest_flux=None):
+                nest_feedback=None, nest_flux=None, ctas_per_sm=0):
     return Params(float(dt), float(g), float(dry_eps), float(arrival_thr), int(precision),
                   int(schedule), int(tile[0]), int(tile[1]), int(bool(track_velocity)),
                   NEST_RING if nest_feedback is None else int(nest_feedback),
-                  FLUX_LINEAR if nest_flux is None else int(nest_flux))
+                  FLUX_LINEAR if nest_flux is None else int(nest_flux), int(ctas_per_sm))
 
 
 def footprint(blocks, params: Params) -> int:
@@ -149,11 +155,11 @@ class Handle:
 
     def __init__(self, blocks, bathy, manning, dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01,
                  precision=FP64, schedule=SCHED_PERSISTENT, tile=(0, 0), device_mem=None,
-                 track_velocity=False, nest_feedback=None, nest_flux=None):
+                 track_velocity=False, nest_feedback=None, nest_flux=None, ctas_per_sm=0):
         L = lib()
         self.blocks = [dict(b) for b in blocks]
         self.params = make_params(dt, g, dry_eps, arrival_thr, precision, schedule, tile,
-                                  track_velocity, nest_feedback, nest_flux)
+                                  track_velocity, nest_feedback, nest_flux, ctas_per_sm)
         self.dt = float(dt)
         nb = len(blocks)
         arr = _blocks_array(blocks)
@@ -174,9 +180,10 @@ class Handle:
     @classmethod
     def from_scenario(cls, sc, precision=FP64, schedule=SCHED_PERSISTENT, tile=(0, 0),
                       device_mem=None, track_velocity=False, nest_feedback=None,
-                      nest_flux=None):
+                      nest_flux=None, ctas_per_sm=0):
         h = cls(sc.blocks, sc.bathy, sc.manning, sc.dt, sc.g, sc.dry_eps, sc.arrival_thr,
-                precision, schedule, tile, device_mem, track_velocity, nest_feedback, nest_flux)
+                precision, schedule, tile, device_mem, track_velocity, nest_feedback, nest_flux,
+                ctas_per_sm)
         for k, dz in enumerate(sc.uplift):
             if dz is not None:
                 h.set_initial_uplift(k, dz)
@@ -278,11 +285,14 @@ class Handle:
 class Batch:
     """Many hierarchies stepped together by one persistent, graph-captured launch."""
 
-    def __init__(self, precision=FP32, schedule=SCHED_PERSISTENT, chunk_steps=50):
+    def __init__(self, precision=FP32, schedule=SCHED_PERSISTENT, chunk_steps=50, tile_y=0,
+                 ctas_per_sm=0):
         out = _vp()
-        rc = lib().rti_batch_create(int(precision), int(schedule), int(chunk_steps), C.byref(out))
+        cfg = BatchConfig(int(precision), int(schedule), int(chunk_steps), int(tile_y),
+                          int(ctas_per_sm))
+        rc = lib().rti_batch_create_ex(C.byref(cfg), C.byref(out))
         if rc:
-            raise RtiError(rc, "rti_batch_create")
+            raise RtiError(rc, "rti_batch_create_ex")
         self._b = out
         self.chunk = int(chunk_steps)
         self.members = []

@@ -109,7 +109,7 @@ def load_sites(kinds=("3level", "4level", "5level"), seed=1000):
 class Server:
     def __init__(self, sites: dict, pool_bytes: int, precision=rti.FP32, chunk_steps: int = 50,
                  schedule=rti.SCHED_PERSISTENT, keep_fields: bool = False,
-                 audit_every: int | None = None):
+                 audit_every: int | None = None, tile_y: int = 0, ctas_per_sm: int = 0):
         import torch
 
         self.torch = torch
@@ -119,7 +119,9 @@ class Server:
         self.audit_every = audit_every
         self.pool = Pool(pool_bytes, torch.empty(int(pool_bytes), dtype=torch.uint8,
                                                  device="cuda"))
-        self.batch = rti.Batch(precision, schedule, chunk_steps)
+        self.tile_y = int(tile_y)
+        self.batch = rti.Batch(precision, schedule, chunk_steps, tile_y=tile_y,
+                               ctas_per_sm=ctas_per_sm)
         self.stream = torch.cuda.Stream()
         self.chunk = chunk_steps
 
@@ -129,7 +131,8 @@ class Server:
         off = self.pool.alloc(req.footprint)
         if off is None:
             return False
-        h = rti.Handle.from_scenario(sc, precision=self.prec, device_mem=self.pool.view(off))
+        h = rti.Handle.from_scenario(sc, precision=self.prec, device_mem=self.pool.view(off),
+                                     tile=(0, self.tile_y))
         self.batch.add(h, req.nsteps)
         live[req.rid] = (req, h, off)
         return True
@@ -261,7 +264,8 @@ class Server:
             nsteps = max(1, int(round(t["hours"] * 3600.0 * time_scale / site.dt)))
             r = Request(i, t["kind"], int(t["seed"]), float(t["hours"]),
                         float(t["arrival_s"]) * time_scale, nsteps)
-            p = rti.make_params(site.dt, site.g, site.dry_eps, site.arrival_thr, prec)
+            p = rti.make_params(site.dt, site.g, site.dry_eps, site.arrival_thr, prec,
+                                tile=(0, self.tile_y))
             r.footprint = rti.footprint(site.blocks, p)
             r.cells = site.cells
             out.append(r)
@@ -286,7 +290,8 @@ class Server:
             if off is None:
                 raise MemoryError(f"request {r.rid} does not fit the pool")
             r.admitted_s = time.perf_counter() - t0
-            h = rti.Handle.from_scenario(sc, precision=precision, device_mem=self.pool.view(off))
+            h = rti.Handle.from_scenario(sc, precision=precision, device_mem=self.pool.view(off),
+                                         tile=(0, self.tile_y))
             h.step(r.nsteps, self.stream)
             out = {}
             for k in range(len(h.blocks)):
