@@ -92,6 +92,10 @@ typedef struct {
   int ctas_per_sm;    /* resident CTAs per SM of the step kernel's grid: 0 = as many as fit
                          (the occupancy limit), else at most this many (a tuning knob; the
                          results do not depend on it) */
+  double velocity_limit; /* m/s; 0 = off (the default). On, every interior face's flux is
+                         also held to |flux| <= velocity_limit x its face depth, after the
+                         front's outflow limit: a velocity limiter that binds only near
+                         wet/dry fronts, where face depths are small. */
 } rti_params;
 
 typedef struct rti_handle rti_handle;
@@ -131,9 +135,12 @@ int rti_get_max_depth(rti_handle* h, int block, double* out);
 int rti_get_max_height(rti_handle* h, int block, double* out);
 int rti_get_arrival_time(rti_handle* h, int block, double* out);
 /* Maximum water velocity (Sec. IV-A names it among the outputs of the time loop; the
- * formula is this library's reading): the largest cell-centre speed
- * sqrt(((Mw + Me)/2)^2 + ((Ns + Nn)/2)^2) / (h + eta) over the initial state and every
- * state a step finished with, on wet cells (h + eta > dry_eps), m/s, 0 if never wet.
+ * formula is this library's reading): the largest cell-centre speed sqrt(u^2 + v^2) over
+ * the initial state and every state a step finished with, on wet cells
+ * (h + eta > dry_eps), m/s, 0 if never wet. u = (Mw/Dw + Me/De)/2 and v = (Ns/Ds +
+ * Nn/Dn)/2 average the velocities of the cell's four faces, each its flux over its own
+ * depth D_f = (h1 + h2)/2 + (eta1 + eta2)/2 (the edge cell's depth on a block edge;
+ * velocity 0 where D_f <= dry_eps).
  * Needs track_velocity = 1 at create; otherwise RTI_ERR_STATE. */
 int rti_get_max_velocity(rti_handle* h, int block, double* out);
 

@@ -61,7 +61,8 @@ FLUX_LINEAR, FLUX_CONSTANT = 0, 1
 
 class _Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("g", C.c_double), ("dry_eps", C.c_double),
-                ("arrival_thr", C.c_double), ("nest_feedback", C.c_int), ("nest_flux", C.c_int)]
+                ("arrival_thr", C.c_double), ("nest_feedback", C.c_int), ("nest_flux", C.c_int),
+                ("vel_limit", C.c_double)]
 
 
 _libs = {}
@@ -115,7 +116,7 @@ class Oracle:
 
     def __init__(self, blocks, bathy, manning, dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01,
                  lib_path=None, nest_feedback=NEST_RING, nest_flux=FLUX_LINEAR,
-                 parallel=False):
+                 parallel=False, vel_limit=0.0):
         if parallel and lib_path is None:
             build()
             lib_path = LIB_OMP
@@ -135,7 +136,8 @@ class Oracle:
         hp = (C.POINTER(C.c_double) * nb)(*[_dptr(x) for x in self._h])
         npp = (C.POINTER(C.c_float) * nb)(
             *[x.ctypes.data_as(C.POINTER(C.c_float)) for x in self._n])
-        prm = _Params(dt, g, dry_eps, arrival_thr, int(nest_feedback), int(nest_flux))
+        prm = _Params(dt, g, dry_eps, arrival_thr, int(nest_feedback), int(nest_flux),
+                      float(vel_limit))
         err = C.c_int(0)
         self.blocks = [dict(b) for b in blocks]
         self.dt = dt

@@ -66,11 +66,22 @@
  *       when etamax first reaches the threshold (>=).
  *   R10 initial state: eta0 = max(dz, -h) on sea cells, -h on land, fluxes zero.
  *   R11 maximum water velocity (the output update of Sec. IV-A names it; no formula is
- *       given): cell-centre speed of a state, u = (Mw + Me)/2 / D, v = (Ns + Nn)/2 / D with
- *       D = h + eta, kept as its square (u^2 + v^2) / D^2 on wet cells (D > dry_eps). It is
- *       taken from the state each step starts from (the state the previous iteration
- *       finished with), and the read adds the current state, so the result is the maximum
- *       over the initial state and every state a step finished with; 0 if never wet.
+ *       given): cell-centre velocity of a state as the mean of its faces' velocities,
+ *       u = (Mw/Dw + Me/De)/2, v = (Ns/Ds + Nn/Dn)/2, where a face's velocity is its flux
+ *       over its depth D_f = (h1 + h2)/2 + (eta1 + eta2)/2 (the two cells it separates;
+ *       on a block edge the edge cell's own depth), and 0 where D_f <= dry_eps; kept as
+ *       the square u^2 + v^2 on wet cells (D = h + eta > dry_eps). Dividing each face's
+ *       flux by its own depth keeps the speed of a film barely above the wet threshold
+ *       that a neighbour floods at the speed of the flow through its faces; dividing the
+ *       mean flux by the film's depth gave hundreds of m/s. It is taken from the state
+ *       each step starts from (the state the previous iteration finished with), and the
+ *       read adds the current state, so the result is the maximum over the initial state
+ *       and every state a step finished with; 0 if never wet.
+ *   R12 velocity limit (option vel_limit, off by default): after R4's outflow limit, an
+ *       interior face's flux is also held to |flux| <= vel_limit * D_f with D_f the face
+ *       depth of its update (R2, or R4's front depth). In open water it never binds
+ *       (tsunami currents are a few m/s); near a front, where D_f is small, it caps the
+ *       flux that floods or drains a thin layer.
  */
 #include "rti_oracle.h"
 
@@ -162,7 +173,8 @@ orc_state* orc_create(const orc_block* blocks, int nblocks, const double* const*
   int e = ORC_OK;
   if (!blocks || nblocks <= 0 || !bathy || !manning || !p || !(p->dt > 0) || !(p->g > 0) ||
       (p->nest_feedback != ORC_NEST_RING && p->nest_feedback != ORC_NEST_FULL) ||
-      (p->nest_flux != ORC_FLUX_LINEAR && p->nest_flux != ORC_FLUX_CONSTANT))
+      (p->nest_flux != ORC_FLUX_LINEAR && p->nest_flux != ORC_FLUX_CONSTANT) ||
+      !(p->vel_limit >= 0))
     e = ORC_ERR_INVALID_ARG;
   for (int k = 0; e == ORC_OK && k < nblocks; ++k)
     if (!bathy[k] || !manning[k]) e = ORC_ERR_INVALID_ARG;
@@ -225,14 +237,28 @@ static void track_cell(oblk* b, size_t c, long step, const orc_params* p) {
   }
 }
 
+/* R11: depth of the face between cells a and b of the state eta (a == b on a block edge) */
+static double face_depth(const oblk* b, const double* eta, size_t ca, size_t cb) {
+  return 0.5 * (b->h[ca] + b->h[cb]) + 0.5 * (eta[ca] + eta[cb]);
+}
+
+/* R11: velocity across a face of flux q and depth D (0 on a face without water) */
+static double face_velocity(double q, double D, double eps) { return D > eps ? q / D : 0.0; }
+
 /* R11: squared cell-centre speed of cell (i, j) in the state (eta, M, N); -1 if dry */
 static double speed2(const oblk* b, const double* eta, const double* M, const double* N, int i,
                      int j, const orc_params* p) {
-  double D = b->h[C(b, i, j)] + eta[C(b, i, j)];
+  const size_t c = C(b, i, j);
+  double D = b->h[c] + eta[c];
   if (!(D > p->dry_eps)) return -1.0;
-  double u = 0.5 * (M[FX(b, i, j)] + M[FX(b, i + 1, j)]);
-  double v = 0.5 * (N[FY(b, i, j)] + N[FY(b, i, j + 1)]);
-  return (u * u + v * v) / (D * D);
+  const double eps = p->dry_eps;
+  double Dw = face_depth(b, eta, i > 0 ? C(b, i - 1, j) : c, c);
+  double De = face_depth(b, eta, c, i < b->nx - 1 ? C(b, i + 1, j) : c);
+  double Ds = face_depth(b, eta, j > 0 ? C(b, i, j - 1) : c, c);
+  double Dn = face_depth(b, eta, c, j < b->ny - 1 ? C(b, i, j + 1) : c);
+  double u = 0.5 * (face_velocity(M[FX(b, i, j)], Dw, eps) + face_velocity(M[FX(b, i + 1, j)], De, eps));
+  double v = 0.5 * (face_velocity(N[FY(b, i, j)], Ds, eps) + face_velocity(N[FY(b, i, j + 1)], Dn, eps));
+  return u * u + v * v;
 }
 
 /* R11 output update: the state a step starts from */
@@ -477,9 +503,15 @@ static double flux_update(double m, double across, double Df, double grad, doubl
 }
 
 /* R4: a face may carry out of its upwind cell at most a quarter of that cell's water
- * per step (|flux| <= D_src dx / (4 dt)), so four faces cannot drain a cell below dry. */
-static double limit_outflow(double m, double Dlo, double Dhi, double dx, double dt) {
+ * per step (|flux| <= D_src dx / (4 dt)), so four faces cannot drain a cell below dry.
+ * R12 (option): nor more than vel_limit times its face depth Df (a velocity limit). */
+static double limit_outflow(double m, double Dlo, double Dhi, double Df, double dx, double dt,
+                            double vel_limit) {
   double cap = (m > 0 ? Dlo : Dhi) * dx / (4.0 * dt);
+  if (vel_limit > 0) {
+    double vc = vel_limit * Df;
+    if (vc < cap) cap = vc;
+  }
   if (m > cap) return cap;
   if (m < -cap) return -cap;
   return m;
@@ -519,7 +551,7 @@ static double xmom(const oblk* b, int f, int j, const orc_params* p) {
   double nf = b->n[L] > b->n[R] ? b->n[L] : b->n[R];
   double m1 = flux_update(m, nbar_x(b, f, j), Df, grad, adv, nf, b->dtdx, p);
   if (!(wL && wR) && (wL ? m1 < 0.0 : m1 > 0.0)) return 0.0; /* no flow out of a dry cell */
-  return limit_outflow(m1, hL + eL, hR + eR, b->dx, p->dt);
+  return limit_outflow(m1, hL + eL, hR + eR, Df, b->dx, p->dt, p->vel_limit);
 }
 
 /* R3 + R4 at interior y-face (i,g), 1 <= g <= ny-1: R2 with x and y exchanged */
@@ -556,7 +588,7 @@ static double ymom(const oblk* b, int i, int g, const orc_params* p) {
   double nf = b->n[S] > b->n[Nc] ? b->n[S] : b->n[Nc];
   double v1 = flux_update(v, mbar_y(b, i, g), Df, grad, adv, nf, b->dtdx, p);
   if (!(wS && wN) && (wS ? v1 < 0.0 : v1 > 0.0)) return 0.0; /* no flow out of a dry cell */
-  return limit_outflow(v1, hS + eS, hN + eN, b->dx, p->dt);
+  return limit_outflow(v1, hS + eS, hN + eN, Df, b->dx, p->dt, p->vel_limit);
 }
 
 /* R6: radiation flux leaving through an edge next to cell c (sign: +1 east/north) */

@@ -51,6 +51,8 @@ typedef struct {
   double arrival_thr; /* m: arrival when max eta first reaches this */
   int nest_feedback;  /* ORC_NEST_RING or ORC_NEST_FULL */
   int nest_flux;      /* ORC_FLUX_LINEAR or ORC_FLUX_CONSTANT */
+  double vel_limit;   /* m/s: |flux| <= vel_limit * face depth at every interior face
+                         (R12); 0 = no limit */
 } orc_params;
 
 typedef struct orc_state orc_state;
@@ -77,7 +79,8 @@ int orc_get_max_depth(const orc_state* s, int block, double* out);
 /* seconds, -1 if max eta never reached the threshold */
 int orc_get_arrival_time(const orc_state* s, int block, double* out);
 /* R11: max over the initial state and every finished step of the cell-centre speed
- * sqrt(((Mw+Me)/2)^2 + ((Ns+Nn)/2)^2) / (h + eta) on wet cells, m/s (0 if never wet) */
+ * sqrt(u^2 + v^2), u = (Mw/Dw + Me/De)/2, v = (Ns/Ds + Nn/Dn)/2 with D_f the depth of each
+ * face (0 velocity on a face without water), on wet cells, m/s (0 if never wet) */
 int orc_get_max_velocity(const orc_state* s, int block, double* out);
 /* out[0] = water volume sum (h+eta) dx^2, out[1] = cumulative volume that left through
  * the block boundary, out[2] = cumulative volume added by the dry clip, out[3] = cumulative

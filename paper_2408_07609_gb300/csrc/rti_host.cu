@@ -106,7 +106,7 @@ int validate(const rti_block* bl, int nb, const rti_params* p, std::string* why)
       (p->precision != RTI_FP32 && p->precision != RTI_FP64) ||
       (p->schedule != RTI_SCHED_PERSISTENT && p->schedule != RTI_SCHED_PER_PASS) ||
       (p->tile_x != 0 && p->tile_x != kStripW) || p->tile_y < 0 || p->tile_y % 8 ||
-      p->ctas_per_sm < 0 ||
+      p->ctas_per_sm < 0 || !(p->velocity_limit >= 0) ||
       (p->track_velocity != 0 && p->track_velocity != 1) ||
       (p->nest_feedback != RTI_NEST_RING && p->nest_feedback != RTI_NEST_FULL) ||
       (p->nest_flux != RTI_FLUX_LINEAR && p->nest_flux != RTI_FLUX_CONSTANT)) {
@@ -283,6 +283,7 @@ Blk<T> make_blk(rti_handle* h, int k, int base_index, int scen, int child_first,
   b.thr = (T)p.arrival_thr;
   b.dx = (T)dx;
   b.q4dt = (T)(4.0 * dt);
+  b.vlim = p.velocity_limit > 0 ? (T)p.velocity_limit : (T)INFINITY;
   b.dx2 = dx * dx;
   b.vol = dt * dx;
   b.eps_d = p.dry_eps;
@@ -642,15 +643,15 @@ __global__ void k_dense_from_plane(const T* plane, int nx, int ny, int pitch, do
   }
 }
 
-// squared cell-centre speed of a state (R11), -1 on a dry cell
+// R11: velocity across a face of flux q and depth D (0 on a face without water)
 template <class T>
-__device__ __forceinline__ T cell_speed2(T Mw, T Me, T Ns, T Nn, T D, T eps) {
-  if (!(D > eps)) return T(-1);
-  const T u = T(0.5) * (Mw + Me), v = T(0.5) * (Ns + Nn);
-  return (u * u + v * v) / (D * D);
+__device__ __forceinline__ T face_velocity(T q, T D, T eps) {
+  return D > eps ? q / D : T(0);
 }
 
 // maximum water velocity of a block: the running maximum, with the current state added
+// (R11: the mean of the four face velocities, each flux over its face's depth; a block
+// edge's face has the edge cell's depth)
 template <class T>
 __global__ void k_max_velocity(const T* vmax, const T* eta, const T* M, const T* N, const T* hpl,
                                int nx, int ny, int pitch, T eps, double* out) {
@@ -660,8 +661,19 @@ __global__ void k_max_velocity(const T* vmax, const T* eta, const T* M, const T*
     const int r = (int)(i / nx), c = (int)(i - (long long)r * nx);
     const size_t o = (size_t)(r + kYOff) * pitch + (c + kXOff);
     T m = vmax[o];
-    const T s2 = cell_speed2(M[o], M[o + 1], N[o], N[o + pitch], hpl[o] + eta[o], eps);
-    if (s2 > m) m = s2;
+    const T h = hpl[o], e = eta[o], D = h + e;
+    if (D > eps) {
+      const size_t w = c > 0 ? o - 1 : o, ea = c < nx - 1 ? o + 1 : o;
+      const size_t s = r > 0 ? o - pitch : o, no = r < ny - 1 ? o + pitch : o;
+      const T Dw = T(0.5) * (hpl[w] + h) + T(0.5) * (eta[w] + e);
+      const T De = T(0.5) * (h + hpl[ea]) + T(0.5) * (e + eta[ea]);
+      const T Ds = T(0.5) * (hpl[s] + h) + T(0.5) * (eta[s] + e);
+      const T Dn = T(0.5) * (h + hpl[no]) + T(0.5) * (e + eta[no]);
+      const T u = T(0.5) * (face_velocity(M[o], Dw, eps) + face_velocity(M[o + 1], De, eps));
+      const T v = T(0.5) * (face_velocity(N[o], Ds, eps) + face_velocity(N[o + pitch], Dn, eps));
+      const T s2 = u * u + v * v;
+      if (s2 > m) m = s2;
+    }
     out[i] = sqrt((double)m);
   }
 }
@@ -1484,6 +1496,7 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
   b.thr = (T)p->arrival_thr;
   b.dx = (T)g->dx;
   b.q4dt = (T)(4.0 * p->dt);
+  b.vlim = p->velocity_limit > 0 ? (T)p->velocity_limit : (T)INFINITY;
   b.dx2 = g->dx * g->dx;
   b.vol = p->dt * g->dx;
   b.eps_d = p->dry_eps;

@@ -269,21 +269,21 @@ template <class T>
 struct MomK;
 template <>
 struct MomK<double> {
-  double eps, dtdx, g, cfric, dx, q4dt;
+  double eps, dtdx, g, cfric, dx, q4dt, vlim;
 };
 template <>
 struct MomK<float> {
-  float eps, dtdx, gdtdx /* g dt/dx */, cfric, dxq /* dx / (4 dt) */;
+  float eps, dtdx, gdtdx /* g dt/dx */, cfric, dxq /* dx / (4 dt) */, vlim;
 };
 template <class T>
 __device__ __forceinline__ MomK<T> mom_consts(const Blk<T>& b);
 template <>
 __device__ __forceinline__ MomK<double> mom_consts(const Blk<double>& b) {
-  return MomK<double>{b.eps, b.dtdx, b.g, b.cfric, b.dx, b.q4dt};
+  return MomK<double>{b.eps, b.dtdx, b.g, b.cfric, b.dx, b.q4dt, b.vlim};
 }
 template <>
 __device__ __forceinline__ MomK<float> mom_consts(const Blk<float>& b) {
-  return MomK<float>{b.eps, b.dtdx, b.g * b.dtdx, b.cfric, b.dx / b.q4dt};
+  return MomK<float>{b.eps, b.dtdx, b.g * b.dtdx, b.cfric, b.dx / b.q4dt, b.vlim};
 }
 
 template <class T>
@@ -303,14 +303,17 @@ struct Ar<double> {
     double F = K.cfric * nf * nf * sqrt(m * m + across * across) / (Df * Df * cube_root_nr(Df));
     return ((1.0 - F) * m - adv - P) / (1.0 + F);
   }
-  // squared cell-centre speed (u^2 + v^2) / D^2 (R11)
-  static __device__ __forceinline__ double speed2(double u, double v, double D) {
-    return (u * u + v * v) / (D * D);
+  // R11: velocity across a face of flux q and depth D (0 on a face without water)
+  static __device__ __forceinline__ double face_vel(double q, double D, double eps) {
+    return D > eps ? q / D : 0.0;
   }
-  // Outflow limit: |flux| <= D dx / (4 dt) with D the depth of the cell it drains.
-  static __device__ __forceinline__ double limit(double m, double Dlo, double Dhi,
+  // Outflow limit: |flux| <= D dx / (4 dt) with D the depth of the cell it drains, and
+  // the velocity limit |flux| <= vlim Df (vlim = +inf when off, which leaves the cap).
+  static __device__ __forceinline__ double limit(double m, double Dlo, double Dhi, double Df,
                                                  const MomK<double>& K) {
-    const double cap = (m > 0.0 ? Dlo : Dhi) * K.dx / K.q4dt;
+    double cap = (m > 0.0 ? Dlo : Dhi) * K.dx / K.q4dt;
+    const double vc = K.vlim * Df;
+    if (vc < cap) cap = vc;
     if (m > cap) return cap;
     if (m < -cap) return -cap;
     return m;
@@ -333,12 +336,12 @@ struct Ar<float> {
         (K.cfric * nf * nf) * ex2_approx(0.5f * lg2_approx(s2) - 2.33333333f * lg2_approx(Df));
     return __fdividef((1.0f - F) * m - adv - P, 1.0f + F);
   }
-  static __device__ __forceinline__ float speed2(float u, float v, float D) {
-    return __fdividef(u * u + v * v, D * D);
+  static __device__ __forceinline__ float face_vel(float q, float D, float eps) {
+    return D > eps ? __fdividef(q, D) : 0.0f;
   }
-  static __device__ __forceinline__ float limit(float m, float Dlo, float Dhi,
+  static __device__ __forceinline__ float limit(float m, float Dlo, float Dhi, float Df,
                                                 const MomK<float>& K) {
-    const float cap = (m > 0.0f ? Dlo : Dhi) * K.dxq;
+    const float cap = fminf((m > 0.0f ? Dlo : Dhi) * K.dxq, K.vlim * Df);
     if (m > cap) return cap;  // (a NaN passes through, for the non-finite check)
     if (m < -cap) return -cap;
     return m;
@@ -388,7 +391,8 @@ template <class T>
 struct Raw {
   T e, h, m, nn, em;
   float nm;
-  T vm;  // squared-speed maximum (velocity tracking only)
+  T vm;      // squared-speed maximum (velocity tracking only)
+  T eN, hN;  // eta^n and h of cell (c, r + 1) (velocity tracking only)
 };
 
 // The march's input rows are staged ahead in shared memory: a ring of kRingD slots per
@@ -527,7 +531,7 @@ __device__ __forceinline__ T xmom_r(T hL, T eL, T hR, T eR, T m, T nb, bool okm,
   const T nf = (T)(nL > nR ? nL : nR);
   const T m1 = Ar<T>::update(m, nb, Df, grad, adv, nf, K);
   const bool keep = (both || oneL || oneR) && Df > eps && (both || (wL ? !(m1 < T(0)) : !(m1 > T(0))));
-  const T lim = Ar<T>::limit(m1, hL + eL, hR + eR, K);
+  const T lim = Ar<T>::limit(m1, hL + eL, hR + eR, Df, K);
   return keep ? lim : T(0);
 }
 
@@ -550,7 +554,7 @@ __device__ __forceinline__ T ymom_r(T hS, T eS, T hN, T eN, T v, T mb, bool okm,
   const T nf = (T)(nS > nN ? nS : nN);
   const T v1 = Ar<T>::update(v, mb, Df, grad, adv, nf, K);
   const bool keep = (both || oneS || oneN) && Df > eps && (both || (wS ? !(v1 < T(0)) : !(v1 > T(0))));
-  const T lim = Ar<T>::limit(v1, hS + eS, hN + eN, K);
+  const T lim = Ar<T>::limit(v1, hS + eS, hN + eN, Df, K);
   return keep ? lim : T(0);
 }
 
@@ -571,7 +575,7 @@ __device__ __forceinline__ T mom_open(T hA, T eA, T hB, T eB, T m, T across, T p
   const T adv = K.dtdx * (a1 + a2);
   const T nf = (T)(nA > nB ? nA : nB);
   const T m1 = Ar<T>::update(m, across, Df, grad, adv, nf, K);
-  const T lim = Ar<T>::limit(m1, hA + eA, hB + eB, K);
+  const T lim = Ar<T>::limit(m1, hA + eA, hB + eB, Df, K);
   return Df > K.eps ? lim : T(0);
 }
 
@@ -742,6 +746,7 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     cp_async_commit();
   }
   Row<T> A = {}, B = {}, C = {};
+  T e_prev = T(0);  // eta^n of cell (c, r - 1) (velocity tracking only)
 
   // One row r from its inputs `cur`: X receives row r; Y, Z are rows r - 2, r - 1.
   auto row = [&](const Raw<T>& cur, Row<T>& X, const Row<T>& Y, const Row<T>& Z, int r) {
@@ -758,11 +763,23 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     const T nnL = __shfl_up_sync(full, nn, 1);
     const bool own = own_col && r >= y0 && r < ye;
     if (kTrack) {  // R11: the state this step starts from (eta^n, M^n, N^n)
+      // each face's velocity over that face's depth; a block edge's face has the edge
+      // cell's depth (its neighbour taken as the cell itself)
+      const T eW = __shfl_up_sync(full, cur.e, 1), hW = __shfl_up_sync(full, cur.h, 1);
+      const T eE = __shfl_down_sync(full, cur.e, 1), hE = __shfl_down_sync(full, cur.h, 1);
+      const bool w_in = c > 0, e_in = c < nx - 1, s_in = r > 0, n_in = r < ny - 1;
+      const T Dw = T(0.5) * ((w_in ? hW : cur.h) + cur.h) + T(0.5) * ((w_in ? eW : cur.e) + cur.e);
+      const T De = T(0.5) * (cur.h + (e_in ? hE : cur.h)) + T(0.5) * (cur.e + (e_in ? eE : cur.e));
+      const T Ds = T(0.5) * ((s_in ? Z.H : cur.h) + cur.h) + T(0.5) * ((s_in ? e_prev : cur.e) + cur.e);
+      const T Dn = T(0.5) * (cur.h + (n_in ? cur.hN : cur.h)) + T(0.5) * (cur.e + (n_in ? cur.eN : cur.e));
       const T D = cur.h + cur.e;
       if (own && D > eps) {
-        const T s2 = Ar<T>::speed2(T(0.5) * (m + Nw.mE), T(0.5) * (nS + nn), D);
+        const T u = T(0.5) * (Ar<T>::face_vel(m, Dw, eps) + Ar<T>::face_vel(Nw.mE, De, eps));
+        const T v = T(0.5) * (Ar<T>::face_vel(nS, Ds, eps) + Ar<T>::face_vel(nn, Dn, eps));
+        const T s2 = u * u + v * v;
         if (s2 > cur.vm) vmax[o] = s2;
       }
+      e_prev = cur.e;
     }
     T e = cur.e - (dtdx * (Nw.mE - m) + dtdx * (nn - nS));
     const bool clipped = Nw.H + e < T(0);
@@ -883,9 +900,15 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
                          vmax, rowbase + (kRingD - 2) * pitch, pitch, SL,
                          r + kRingD - 2 <= ye);
     cp_async_commit();
-    cp_async_wait<kRingD - 2>();  // row r has landed
-    __syncwarp();                 // ... for every lane's chunks
-    const Raw<T> cur = read_row<T, kTrack>(ws.ring[slot], lane);
+    if (kTrack) cp_async_wait<kRingD - 3>();  // rows r and r + 1 have landed
+    else cp_async_wait<kRingD - 2>();         // row r has landed
+    __syncwarp();                             // ... for every lane's chunks
+    Raw<T> cur = read_row<T, kTrack>(ws.ring[slot], lane);
+    if (kTrack) {
+      const RingSlot<T>& nx1 = ws.ring[(slot + 1) & (kRingD - 1)];
+      cur.eN = nx1.e[lane + 2];
+      cur.hN = nx1.h[lane + 2];
+    }
     slot = (slot + 1) & (kRingD - 1);
     rowbase += pitch;
     Row<T> X;

@@ -54,6 +54,7 @@ struct Blk {
   int* status;     // the owning handle's device status word
   // constants in the state precision (all exactly the values the oracle uses in FP64)
   T dtdx, dt, g, cfric /* 0.5*dt*g */, eps, thr, dx, q4dt /* 4*dt */;
+  T vlim;  // velocity limit of the fluxes (m/s), +inf when off
   // binary64 constants for the nesting sums and the budget
   double dx2, vol /* dt*dx */, eps_d;
 #ifdef RTI_CHECKED

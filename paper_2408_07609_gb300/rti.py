@@ -39,7 +39,8 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("g", C.c_double), ("dry_eps", C.c_double),
                 ("arrival_thr", C.c_double), ("precision", C.c_int), ("schedule", C.c_int),
                 ("tile_x", C.c_int), ("tile_y", C.c_int), ("track_velocity", C.c_int),
-                ("nest_feedback", C.c_int), ("nest_flux", C.c_int), ("ctas_per_sm", C.c_int)]
+                ("nest_feedback", C.c_int), ("nest_flux", C.c_int), ("ctas_per_sm", C.c_int),
+                ("velocity_limit", C.c_double)]
 
 
 class BatchConfig(C.Structure):
@@ -134,11 +135,12 @@ def _blocks_array(blocks):
 
 def make_params(dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01, precision=FP64,
                 schedule=SCHED_PERSISTENT, tile=(0, 0), track_velocity=False,
-                nest_feedback=None, nest_flux=None, ctas_per_sm=0):
+                nest_feedback=None, nest_flux=None, ctas_per_sm=0, velocity_limit=0.0):
     return Params(float(dt), float(g), float(dry_eps), float(arrival_thr), int(precision),
                   int(schedule), int(tile[0]), int(tile[1]), int(bool(track_velocity)),
                   NEST_RING if nest_feedback is None else int(nest_feedback),
-                  FLUX_LINEAR if nest_flux is None else int(nest_flux), int(ctas_per_sm))
+                  FLUX_LINEAR if nest_flux is None else int(nest_flux), int(ctas_per_sm),
+                  float(velocity_limit))
 
 
 def footprint(blocks, params: Params) -> int:
@@ -155,11 +157,13 @@ class Handle:
 
     def __init__(self, blocks, bathy, manning, dt, g=9.81, dry_eps=1e-3, arrival_thr=0.01,
                  precision=FP64, schedule=SCHED_PERSISTENT, tile=(0, 0), device_mem=None,
-                 track_velocity=False, nest_feedback=None, nest_flux=None, ctas_per_sm=0):
+                 track_velocity=False, nest_feedback=None, nest_flux=None, ctas_per_sm=0,
+                 velocity_limit=0.0):
         L = lib()
         self.blocks = [dict(b) for b in blocks]
         self.params = make_params(dt, g, dry_eps, arrival_thr, precision, schedule, tile,
-                                  track_velocity, nest_feedback, nest_flux, ctas_per_sm)
+                                  track_velocity, nest_feedback, nest_flux, ctas_per_sm,
+                                  velocity_limit)
         self.dt = float(dt)
         nb = len(blocks)
         arr = _blocks_array(blocks)
@@ -180,10 +184,10 @@ class Handle:
     @classmethod
     def from_scenario(cls, sc, precision=FP64, schedule=SCHED_PERSISTENT, tile=(0, 0),
                       device_mem=None, track_velocity=False, nest_feedback=None,
-                      nest_flux=None, ctas_per_sm=0):
+                      nest_flux=None, ctas_per_sm=0, velocity_limit=0.0):
         h = cls(sc.blocks, sc.bathy, sc.manning, sc.dt, sc.g, sc.dry_eps, sc.arrival_thr,
                 precision, schedule, tile, device_mem, track_velocity, nest_feedback, nest_flux,
-                ctas_per_sm)
+                ctas_per_sm, velocity_limit)
         for k, dz in enumerate(sc.uplift):
             if dz is not None:
                 h.set_initial_uplift(k, dz)

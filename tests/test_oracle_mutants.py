@@ -54,6 +54,9 @@ MUTANTS = [
      "for (int y = 3 * J + 1; y < 3 * J + 4 && y < c->ny; ++y) { /* inner"),
     ("front: outflow limit of half a cell", "double cap = (m > 0 ? Dlo : Dhi) * dx / (4.0 * dt);",
      "double cap = (m > 0 ? Dlo : Dhi) * dx / (2.0 * dt);"),
+    ("front: velocity limit on the still-water depth",
+     "    double vc = vel_limit * Df;", "    double vc = vel_limit * (0.5 * (Dlo + Dhi));"),
+    ("front: velocity limit ignored", "    if (vc < cap) cap = vc;", "    (void)vc;"),
     ("front: outflow limit on the downwind cell", "double cap = (m > 0 ? Dlo : Dhi) * dx / (4.0 * dt);",
      "double cap = (m > 0 ? Dhi : Dlo) * dx / (4.0 * dt);"),
     ("initial: no floor at the ground", "      if (e < -h) e = -h;\n    } else {",
@@ -82,12 +85,16 @@ MUTANTS = [
     ("outputs: strict arrival threshold", "e >= p->arrival_thr", "e > p->arrival_thr"),
     ("outputs: max tracked on dry cells", "if (b->h[c] + e > p->dry_eps && e > b->emax[c])",
      "if (e > b->emax[c])"),
-    ("velocity: west face only", "double u = 0.5 * (M[FX(b, i, j)] + M[FX(b, i + 1, j)]);",
-     "double u = M[FX(b, i, j)];"),
-    ("velocity: speed without the depth", "return (u * u + v * v) / (D * D);",
-     "return (u * u + v * v);"),
-    ("velocity: y faces of the wrong row", "double v = 0.5 * (N[FY(b, i, j)] + N[FY(b, i, j + 1)]);",
-     "double v = 0.5 * (N[FY(b, i, j)] + N[FY(b, i, j)]);"),
+    ("velocity: west face only",
+     "double u = 0.5 * (face_velocity(M[FX(b, i, j)], Dw, eps) + face_velocity(M[FX(b, i + 1, j)], De, eps));",
+     "double u = face_velocity(M[FX(b, i, j)], Dw, eps);"),
+    ("velocity: speed without the depth", "return D > eps ? q / D : 0.0;",
+     "return D > eps ? q : 0.0;"),
+    ("velocity: y faces of the wrong row", "face_velocity(N[FY(b, i, j + 1)], Dn, eps)",
+     "face_velocity(N[FY(b, i, j)], Dn, eps)"),
+    ("velocity: the cell's depth for every face",
+     "double Dw = face_depth(b, eta, i > 0 ? C(b, i - 1, j) : c, c);",
+     "double Dw = D;"),
     ("velocity: not a running maximum", "if (s2 > b->vmax2[C(b, i, j)]) b->vmax2[C(b, i, j)] = s2;",
      "b->vmax2[C(b, i, j)] = s2 > 0 ? s2 : 0.0;"),
 ]
@@ -98,9 +105,11 @@ BATTERY = [
     pins.test_cube_root_is_within_four_ulp,
     pins.test_max_velocity_averages_the_two_faces_of_a_cell,
     pins.test_max_velocity_of_uniform_flow_is_exact,
+    pins.test_max_velocity_takes_each_face_over_its_own_depth,
     pins.test_max_velocity_is_zero_at_rest_and_on_dry_land_and_grows_monotonically,
     pins.test_max_and_arrival_are_functions_of_history,
     pins.test_outflow_limit_on_a_puddle,
+    pins.test_velocity_limit_on_a_puddle,
     pins.test_advective_depth_is_the_new_level,
     pins.test_initial_condition_r10,
     pins.test_nest_constant_field_ring_average,

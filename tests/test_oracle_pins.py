@@ -650,6 +650,28 @@ def test_max_velocity_averages_the_two_faces_of_a_cell(oracle_mod):
     assert np.array_equal(o.max_velocity(0), v)
 
 
+def test_max_velocity_takes_each_face_over_its_own_depth(oracle_mod):
+    """R11 divides each face's flux by that face's depth: over a bottom deepening by 1 m a
+    cell (h_i = 2 + i, eta = 0) with a uniform x-flux of 1 m^2/s between walls, face f lies
+    between depths 1 + f and 2 + f, so its depth is 1.5 + f and the cell-centre speed is
+    (1/(1.5 + i) + 1/(2.5 + i))/2, with 0 for a wall face (whose depth is the edge cell's);
+    the mean flux over the cell's depth, 1/(2 + i), differs."""
+    nx, ny = 12, 3
+    blk = dict(level=1, parent=-1, nx=nx, ny=ny, i0=0, j0=0, dx=100.0, bc=(0, 0, 0, 0))
+    h = np.tile(2.0 + np.arange(nx, dtype=float), (ny, 1))
+    o = oracle_mod.Oracle([blk], [h], [np.zeros((ny, nx), np.float32)], dt=1.0)
+    M = np.ones((ny, nx + 1))
+    M[:, 0] = M[:, nx] = 0.0
+    o.set_state(0, eta=np.zeros((ny, nx)), M=M, N=np.zeros((ny + 1, nx)))
+    i = np.arange(nx, dtype=float)
+    uw = np.where(i > 0, 1.0 / (1.5 + i), 0.0)
+    ue = np.where(i < nx - 1, 1.0 / (2.5 + i), 0.0)
+    want = np.tile(0.5 * (uw + ue), (ny, 1))
+    got = o.max_velocity(0)
+    assert np.allclose(got, want, rtol=1e-15, atol=0)
+    assert not np.allclose(got[:, 1:-1], 1.0 / (2.0 + i[1:-1]), rtol=1e-3)
+
+
 def test_max_velocity_is_zero_at_rest_and_on_dry_land_and_grows_monotonically(oracle_mod):
     """Lake at rest: 0 everywhere. After a source: a running maximum (never decreases
     between reads), positive where the wave passed, 0 on land that never got wet."""
@@ -755,6 +777,71 @@ def test_outflow_limit_on_a_puddle(oracle_mod):
         assert np.isclose(depth[j, i], q, rtol=1e-12, atol=0)
     b = o.budget(0)
     assert b["clip"] <= 1e-15 and abs(b["volume"] - v0) <= 1e-12 * v0
+
+
+def test_velocity_limit_on_a_puddle(oracle_mod):
+    """R12, the optional velocity limit: an interior face's flux is held to
+    |flux| <= vel_limit x its face depth after the outflow limit. On the draining puddle of
+    the outflow-limit pin the four front faces have the front depth D_f = eta_wet + h_dry
+    = 0.1 m; with vel_limit = 0.1 m/s each carries exactly 0.1 x 0.1 = 0.01 m^2/s out
+    (below the outflow limit's 0.025), so after the second mass update the puddle holds
+    0.1 - 4 x 0.01 = 0.06 m and each neighbour 0.01 m; with the limit off the outflow
+    limit decides, as in that pin. Volume is conserved and nothing is clipped."""
+    nx = ny = 5
+    blk, hh, nn = single(nx, ny, 1.0, -1.0)
+    eta = np.full((ny, nx), 1.0)
+    eta[2, 2] = 1.1
+    for vlim, q in ((0.1, 0.01), (0.0, 0.025)):
+        o = oracle_mod.Oracle([blk], [hh], [nn], dt=1.0, vel_limit=vlim)
+        o.set_state(0, eta=eta)
+        v0 = o.budget(0)["volume"]
+        o.step(1)
+        _, M, N = o.get_state(0)
+        for got, sign in ((M[2, 3], 1), (M[2, 2], -1), (N[3, 2], 1), (N[2, 2], -1)):
+            assert np.isclose(got, sign * q, rtol=1e-14, atol=0), (vlim, got)
+        o.step(1)
+        depth = o.get_state(0)[0] + hh
+        assert np.isclose(depth[2, 2], 0.1 - 4 * q, rtol=1e-12, atol=1e-15)
+        for (j, i) in ((2, 1), (2, 3), (1, 2), (3, 2)):
+            assert np.isclose(depth[j, i], q, rtol=1e-12, atol=0)
+        b = o.budget(0)
+        assert b["clip"] <= 1e-15 and abs(b["volume"] - v0) <= 1e-12 * v0
+
+
+def test_velocity_limit_leaves_open_water_alone_and_closes_the_budget(oracle_mod):
+    """A 20 m/s limit never binds in open water (a 3 m wave on a 50 m shelf moves at about
+    1 m/s): the open-water run with the limit on equals the run without it, bitwise;
+    with a limit of 0.5 m/s it binds at the beach and the nested budget still closes."""
+    from paper_2408_07609_gb300 import scenarios as S
+
+    sc = S.coastal_hierarchy("vl", 5, (60, 54, 810.0), [(1, 36, 36), (1, 27, 27)], dt=0.5,
+                             steps=0, shelf_w=8e3, slope_w=10e3, wiggle=1e3, coast_frac=0.6,
+                             land_frac=0.4, source=dict(kind="gauss", sigma=4e3, peak=2.0))
+    blk, hh, nn = single(40, 30, 500.0, 50.0, n=0.025, bc=(0, 0, 0, 0))
+    x = centres(40, 500.0)
+    y = centres(30, 500.0)
+    bump = 3.0 * np.exp(-((x[None, :] - 10e3) ** 2 + (y[:, None] - 7e3) ** 2) / (2 * 2e3 ** 2))
+    runs = []
+    for vlim in (0.0, 20.0):
+        o = oracle_mod.Oracle([blk], [hh], [nn], dt=5.0, vel_limit=vlim)
+        o.set_initial_uplift(0, bump)
+        o.step(200)
+        runs.append(o.get_state(0))
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+    o = oracle_mod.Oracle(sc.blocks, sc.bathy, sc.manning, sc.dt, vel_limit=0.5)
+    r = oracle_mod.Oracle(sc.blocks, sc.bathy, sc.manning, sc.dt)
+    for oo in (o, r):
+        for k, dz in enumerate(sc.uplift):
+            if dz is not None:
+                oo.set_initial_uplift(k, dz)
+    v0 = [o.budget(k)["volume"] for k in range(3)]
+    o.step(1500)
+    r.step(1500)
+    for k in range(3):
+        b = o.budget(k)
+        assert abs(b["volume"] - (v0[k] - b["outflow"] + b["clip"] + b["ring"])) <= 1e-12 * v0[k]
+    assert any(not np.array_equal(o.get_state(k)[1], r.get_state(k)[1]) for k in range(3))
 
 
 def test_full_feedback_exchange_is_simultaneous(oracle_mod):
