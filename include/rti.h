@@ -127,6 +127,10 @@ int rti_step(rti_handle* h, int nsteps, void* stream);
 
 /* Wait for the handle's enqueued work and return its device status. */
 int rti_sync(rti_handle* h);
+/* Host watchdog: wait at most `seconds` for the handle's enqueued work, polling without a
+ * blocking device call. RTI_ERR_TIMEOUT if it has not finished by then (the work stays
+ * enqueued; a later wait picks it up), else what rti_sync returns. */
+int rti_sync_timeout(rti_handle* h, double seconds);
 
 /* Outputs of one block, nx*ny doubles into caller memory; each waits for enqueued work.
  * max depth = h + max eta over wet instants (0 if never wet); max height = max eta over
@@ -149,6 +153,17 @@ int rti_get_max_velocity(rti_handle* h, int block, double* out);
 int rti_get_state(rti_handle* h, int block, double* eta, double* M, double* N);
 int rti_set_state(rti_handle* h, int block, const double* eta, const double* M,
                   const double* N);
+
+/* Checkpoint and resume of the whole handle, bit for bit: the current level of every
+ * block's eta, M and N, its maximum level, arrival steps, speed maximum (when tracked),
+ * budget terms, and the step counter, as raw device bytes in the state precision.
+ * rti_checkpoint_bytes gives the size of the caller's host buffer; rti_checkpoint_save
+ * fills it (waiting for enqueued work); rti_checkpoint_load restores it into a handle
+ * created with the same blocks and params (RTI_ERR_INVALID_ARG otherwise), after which
+ * stepping continues exactly as the saved handle would have. */
+size_t rti_checkpoint_bytes(const rti_handle* h);
+int rti_checkpoint_save(rti_handle* h, void* host_buf, size_t bytes);
+int rti_checkpoint_load(rti_handle* h, const void* host_buf, size_t bytes);
 
 /* Volume budget of one block (binary64): out[0] = water volume sum (h + eta) dx^2,
  * out[1] = cumulative volume that left through the block's boundary faces, out[2] =
@@ -252,6 +267,8 @@ int rti_batch_step(rti_batch* b, void* stream);
 /* steps a member still has to take, as of the enqueued work */
 long long rti_batch_remaining(rti_batch* b, rti_handle* h);
 int rti_batch_sync(rti_batch* b);
+/* rti_batch_sync with the host watchdog of rti_sync_timeout */
+int rti_batch_sync_timeout(rti_batch* b, double seconds);
 void rti_batch_destroy(rti_batch* b);
 
 #ifdef __cplusplus

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -184,8 +185,11 @@ struct Group {
   size_t cap_scen = 0;
   int* d_status = nullptr;
   Bar* d_bar = nullptr;
-  int grid = 0, grid_track = 0, grid_fb = 0;  // co-resident grids of the kernel variants
+  int grid = 0;                  // co-resident grid of the plain variant
+  int grids[kStepModes] = {};    // of every variant (0: not computed yet)
+  int cap = 0;                   // CTAs per SM cap (0 = none)
   bool track = false;            // some member keeps the maximum velocity
+  bool limit = false;            // some member keeps the velocity limit
   long long spin_cycles = kSpinCycles;
   // pinned staging for table uploads
   char* h_stage = nullptr;
@@ -341,16 +345,10 @@ int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, int cap
     long long c = std::atoll(v);
     if (c > 0) g->spin_cycles = c;
   }
-  if (e == cudaSuccess) {
+  g->cap = cap;
+  if (e == cudaSuccess)
     e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid, tx, ty, kStepPlain, cap)
                          : persistent_grid<double>(&g->grid, tx, ty, kStepPlain, cap);
-  if (e == cudaSuccess)
-    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_track, tx, ty, kStepTrack, cap)
-                         : persistent_grid<double>(&g->grid_track, tx, ty, kStepTrack, cap);
-  if (e == cudaSuccess)
-    e = prec == RTI_FP32 ? persistent_grid<float>(&g->grid_fb, tx, ty, kStepFeedback, cap)
-                         : persistent_grid<double>(&g->grid_fb, tx, ty, kStepFeedback, cap);
-  }
   if (e != cudaSuccess) return cuda_err(err, e, "group setup");
   return RTI_OK;
 }
@@ -370,6 +368,7 @@ KParams<T> kparams(Group* g, int nsteps) {
   kp.bar = g->d_bar;
   kp.nsteps = nsteps;
   kp.track = g->track ? 1 : 0;
+  kp.limit = g->limit ? 1 : 0;
   kp.tx = g->tx;
   kp.ty = g->ty;
   kp.spin_cycles = g->spin_cycles;
@@ -403,10 +402,11 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   std::vector<Tile> tiles;
   std::vector<FbItem> fb;
   long long cells = 0;
-  bool track = false;
+  bool track = false, limit = false;
   for (size_t mi = 0; mi < g->members.size(); ++mi) {
     rti_handle* h = g->members[mi];
     track = track || h->params.track_velocity != 0;
+    limit = limit || h->params.velocity_limit > 0;
     const int base = (int)blks.size();
     const int nb = (int)h->blocks.size();
     std::vector<std::vector<int>> ch(nb);
@@ -474,7 +474,8 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   if (e != cudaSuccess) return cuda_err(err, e, "device tables");
   // the captured graph holds the old pointers, the other kernel variant, or launches
   // with or without the feedback phase
-  if ((moved || track != g->track || fb.empty() != (g->nfb == 0)) && g->gexec) {
+  if ((moved || track != g->track || limit != g->limit || fb.empty() != (g->nfb == 0)) &&
+      g->gexec) {
     cudaGraphExecDestroy(g->gexec);
     g->gexec = nullptr;
     g->graph_tried = false;
@@ -524,6 +525,7 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   g->nkids = (int)kids.size();
   g->cells = cells;
   g->track = track;
+  g->limit = limit;
   g->nfb = (int)fb.size();
   g->dirty = false;
   return RTI_OK;
@@ -534,11 +536,20 @@ int group_upload_any(Group* g, cudaStream_t st, std::string* err) {
 }
 
 // grid of the variant a chunk of this group launches (the smallest of the variants a
-// one-launch-per-step chunk uses)
-int launch_grid(const Group* g) {
-  if (g->sched == RTI_SCHED_PERSISTENT)
-    return g->nfb > 0 ? g->grid_fb : (g->track ? g->grid_track : g->grid);
-  return g->track ? g->grid_track : g->grid;
+// one-launch-per-step chunk uses), computed on first use
+int launch_grid(Group* g) {
+  const int lim = g->limit ? kStepLimit : 0;
+  const int mode = (g->sched == RTI_SCHED_PERSISTENT && g->nfb > 0
+                        ? kStepFeedback
+                        : (g->track ? kStepTrack : kStepPlain)) | lim;
+  if (!g->grids[mode]) {
+    int grid = 0;
+    const cudaError_t e =
+        g->prec == RTI_FP32 ? persistent_grid<float>(&grid, g->tx, g->ty, mode, g->cap)
+                            : persistent_grid<double>(&grid, g->tx, g->ty, mode, g->cap);
+    g->grids[mode] = e == cudaSuccess && grid > 0 ? grid : g->grid;
+  }
+  return g->grids[mode];
 }
 
 int launch_any(Group* g, int nsteps, cudaStream_t st, std::string* err) {
@@ -816,6 +827,22 @@ int wait_handle(rti_handle* h) {
   cudaError_t e = cudaEventSynchronize(h->done);
   if (e != cudaSuccess) return cuda_err(&h->err, e, "wait");
   return RTI_OK;
+}
+
+// Poll an event until it completes or `seconds` pass (no blocking device call):
+// RTI_OK, RTI_ERR_TIMEOUT, or RTI_ERR_CUDA.
+int poll_event(cudaEvent_t ev, double seconds, std::string* err) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return RTI_OK;
+    if (e != cudaErrorNotReady) return cuda_err(err, e, "wait");
+    const double dt =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (dt >= seconds)
+      return set_err(err, RTI_ERR_TIMEOUT, "host watchdog: the enqueued work has not finished");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
 }
 
 // initial level and outputs of block k (dz: host binary64 uplift, or null for rest)
@@ -1110,6 +1137,18 @@ int rti_sync(rti_handle* h) {
   return read_status(h->self, h, &h->err);
 }
 
+int rti_sync_timeout(rti_handle* h, double seconds) {
+  if (!h || !(seconds >= 0)) return RTI_ERR_INVALID_ARG;
+  int rc = poll_event(h->done, seconds, &h->err);
+  if (rc) return rc;
+  if (h->batch) {
+    rc = poll_event(h->batch->done, seconds, &h->err);
+    if (rc) return rc;
+    return read_status(&h->batch->g, h, &h->err);
+  }
+  return read_status(h->self, h, &h->err);
+}
+
 static int sync_for_read(rti_handle* h) {
   int rc = wait_handle(h);
   if (rc) return rc;
@@ -1223,6 +1262,96 @@ int rti_get_max_velocity(rti_handle* h, int block, double* out) {
 int rti_get_max_depth(rti_handle* h, int block, double* out) { return get_out(h, block, out, 0); }
 int rti_get_max_height(rti_handle* h, int block, double* out) { return get_out(h, block, out, 1); }
 int rti_get_arrival_time(rti_handle* h, int block, double* out) { return get_out(h, block, out, 2); }
+
+// ---- checkpoints: a header, then per block the raw planes of the current level
+namespace {
+struct CkptHeader {
+  unsigned long long magic;  // 'RTICKPT1'
+  int prec, nblocks, track, pad;
+  long long base;
+  unsigned long long bytes;  // whole checkpoint
+};
+constexpr unsigned long long kCkptMagic = 0x3154504b43495452ULL;
+
+// the (offset, bytes) ranges of block k's checkpointed planes at level p
+void ckpt_ranges(const rti_handle* h, int k, int p, std::vector<std::pair<size_t, size_t>>* out) {
+  const BlkMem& m = h->mem[k];
+  const size_t plane = (size_t)m.pitch * (size_t)m.rows, es = esize(h->prec);
+  out->push_back({m.eta[p], plane * es});
+  out->push_back({m.M[p], plane * es});
+  out->push_back({m.N[p], plane * es});
+  out->push_back({m.emax, plane * es});
+  out->push_back({m.arr, plane * 4});
+  if (m.vmax) out->push_back({m.vmax, plane * es});
+  out->push_back({m.budget, (size_t)m.tiles_x * m.tiles_y * 4 * sizeof(double)});
+}
+
+size_t ckpt_size(const rti_handle* h) {
+  size_t n = sizeof(CkptHeader);
+  std::vector<std::pair<size_t, size_t>> r;
+  for (size_t k = 0; k < h->blocks.size(); ++k) ckpt_ranges(h, (int)k, 0, &r);
+  for (auto& x : r) n += x.second;
+  return n;
+}
+}  // namespace
+
+size_t rti_checkpoint_bytes(const rti_handle* h) { return h ? ckpt_size(h) : 0; }
+
+int rti_checkpoint_save(rti_handle* h, void* host_buf, size_t bytes) {
+  if (!h || !host_buf || bytes < ckpt_size(h)) return RTI_ERR_INVALID_ARG;
+  int rc = sync_for_read(h);
+  if (rc) return rc;
+  CkptHeader hd = {kCkptMagic, h->prec, (int)h->blocks.size(), h->params.track_velocity, 0,
+                   h->base, (unsigned long long)ckpt_size(h)};
+  char* out = static_cast<char*>(host_buf);
+  std::memcpy(out, &hd, sizeof hd);
+  size_t o = sizeof hd;
+  const int p = (int)(h->base & 1);
+  std::vector<std::pair<size_t, size_t>> r;
+  for (size_t k = 0; k < h->blocks.size(); ++k) ckpt_ranges(h, (int)k, p, &r);
+  for (auto& x : r) {
+    cudaError_t e = cudaMemcpy(out + o, h->arena + x.first, x.second, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(&h->err, e, "checkpoint save");
+    o += x.second;
+    h->d2h += (long long)x.second;
+  }
+  return RTI_OK;
+}
+
+int rti_checkpoint_load(rti_handle* h, const void* host_buf, size_t bytes) {
+  if (!h || !host_buf || bytes < sizeof(CkptHeader)) return RTI_ERR_INVALID_ARG;
+  if (h->batch) return set_err(&h->err, RTI_ERR_STATE, "handle is in a batch");
+  CkptHeader hd;
+  std::memcpy(&hd, host_buf, sizeof hd);
+  if (hd.magic != kCkptMagic || hd.prec != h->prec || hd.nblocks != (int)h->blocks.size() ||
+      hd.track != h->params.track_velocity || hd.bytes != ckpt_size(h) || bytes < hd.bytes ||
+      hd.base < 0)
+    return set_err(&h->err, RTI_ERR_INVALID_ARG, "checkpoint of another hierarchy or params");
+  int rc = wait_handle(h);
+  if (rc) return rc;
+  const char* in = static_cast<const char*>(host_buf);
+  size_t o = sizeof hd;
+  const int p = (int)(hd.base & 1);
+  std::vector<std::pair<size_t, size_t>> r;
+  for (size_t k = 0; k < h->blocks.size(); ++k) ckpt_ranges(h, (int)k, p, &r);
+  for (auto& x : r) {
+    cudaError_t e = cudaMemcpy(h->arena + x.first, in + o, x.second, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_err(&h->err, e, "checkpoint load");
+    o += x.second;
+    h->h2d += (long long)x.second;
+  }
+  h->base = hd.base;
+  cudaError_t e = cudaMemset(h->arena + h->off_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->self->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "status reset");
+  h->self->remaining[0] = 0;
+  h->self->dirty = true;
+  rc = group_upload_any(h->self, 0, &h->err);
+  if (rc) return rc;
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(&h->err, e, "checkpoint load");
+  return RTI_OK;
+}
 
 int rti_get_budget(rti_handle* h, int block, double out[4]) {
   if (bad_block(h, block) || !out) return RTI_ERR_INVALID_ARG;
@@ -1393,6 +1522,17 @@ int rti_batch_sync(rti_batch* b) {
   return RTI_OK;
 }
 
+int rti_batch_sync_timeout(rti_batch* b, double seconds) {
+  if (!b || !(seconds >= 0)) return RTI_ERR_INVALID_ARG;
+  int rc = poll_event(b->done, seconds, &b->err);
+  if (rc) return rc;
+  for (rti_handle* h : b->g.members) {
+    rc = read_status(&b->g, h, &h->err);
+    if (rc) return rc;
+  }
+  return RTI_OK;
+}
+
 void rti_batch_destroy(rti_batch* b) {
   if (!b) return;
   cudaEventSynchronize(b->done);
@@ -1507,7 +1647,8 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
   k_noalloc_setup<T><<<1, 256, 0, stream>>>(s, b, tx, ty, tiles_x, tiles_y, steps_done, nsteps);
   cudaError_t e = cudaGetLastError();
   int grid = 0;
-  if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty, kStepPlain, p->ctas_per_sm);
+  const int mode = kStepPlain | (p->velocity_limit > 0 ? kStepLimit : 0);
+  if (e == cudaSuccess) e = persistent_grid<T>(&grid, tx, ty, mode, p->ctas_per_sm);
   if (e == cudaSuccess) {
     KParams<T> kp;
     std::memset(&kp, 0, sizeof(kp));
@@ -1522,6 +1663,7 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
     kp.tx = tx;
     kp.ty = ty;
     kp.spin_cycles = kSpinCycles;
+    kp.limit = p->velocity_limit > 0 ? 1 : 0;
 #ifdef RTI_CHECKED
     kp.nblk = 1;
     kp.nkids = 0;

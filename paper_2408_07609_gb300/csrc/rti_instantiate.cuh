@@ -4,22 +4,32 @@
 
 namespace rti {
 
+namespace {
+// the step kernel of variant `mode` (kStep* base, plus kStepLimit); null for an unused mode
+using StepFn = void (*)(KParams<RTI_T>, int, int);
+StepFn step_kernel(int mode) {
+  switch (mode) {
+    case kStepPlain: return k_step<RTI_T, kStepPlain>;
+    case kStepTrack: return k_step<RTI_T, kStepTrack>;
+    case kStepFeedback: return k_step<RTI_T, kStepFeedback>;
+    case kStepPlain | kStepLimit: return k_step<RTI_T, kStepPlain | kStepLimit>;
+    case kStepTrack | kStepLimit: return k_step<RTI_T, kStepTrack | kStepLimit>;
+    case kStepFeedback | kStepLimit: return k_step<RTI_T, kStepFeedback | kStepLimit>;
+    default: return nullptr;
+  }
+}
+}  // namespace
+
 template <>
 cudaError_t persistent_grid<RTI_T>(int* grid, int tx, int ty, int mode, int cap) {
   (void)tx;
   (void)ty;
+  const StepFn fn = step_kernel(mode);
+  if (!fn) return cudaErrorInvalidValue;
   int dev = 0, sms = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = mode == kStepFeedback
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T, kStepFeedback>,
-                                                            kWarps * 32, 0)
-        : mode == kStepTrack
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T, kStepTrack>,
-                                                            kWarps * 32, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<RTI_T, kStepPlain>,
-                                                            kWarps * 32, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kWarps * 32, 0);
   if (e == cudaSuccess && cap > 0 && per > cap) per = cap;
   if (e == cudaSuccess) *grid = sms * (per > 0 ? per : 1);
   return e;
@@ -29,6 +39,7 @@ template <>
 cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid,
                                 const int* nscen, cudaStream_t st) {
   const dim3 blk(32, kWarps);
+  const int lim = kp.limit ? kStepLimit : 0;
   cudaError_t e = cudaMemsetAsync(kp.bar, 0, sizeof(Bar), st);  // barrier and strip counters
   if (e != cudaSuccess) return e;
   if (schedule == 0) {  // one cooperative launch for the whole chunk
@@ -42,14 +53,13 @@ cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = kp.fb_any  ? cudaLaunchKernelEx(&cfg, k_step<RTI_T, kStepFeedback>, kp, 0, kp.nsteps)
-        : kp.track ? cudaLaunchKernelEx(&cfg, k_step<RTI_T, kStepTrack>, kp, 0, kp.nsteps)
-                   : cudaLaunchKernelEx(&cfg, k_step<RTI_T, kStepPlain>, kp, 0, kp.nsteps);
+    const int mode = (kp.fb_any ? kStepFeedback : kp.track ? kStepTrack : kStepPlain) | lim;
+    e = cudaLaunchKernelEx(&cfg, step_kernel(mode), kp, 0, kp.nsteps);
   } else {  // one launch per step (and one for the full-feedback phase before it)
+    const StepFn fn = step_kernel((kp.track ? kStepTrack : kStepPlain) | lim);
     for (int s = 0; s < kp.nsteps && e == cudaSuccess; ++s) {
       if (kp.fb_any) k_feedback<RTI_T><<<grid, blk, 0, st>>>(kp, s);
-      if (kp.track) k_step<RTI_T, kStepTrack><<<grid, blk, 0, st>>>(kp, s, 1);
-      else k_step<RTI_T, kStepPlain><<<grid, blk, 0, st>>>(kp, s, 1);
+      fn<<<grid, blk, 0, st>>>(kp, s, 1);
       e = cudaGetLastError();
     }
   }

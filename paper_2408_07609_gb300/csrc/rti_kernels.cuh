@@ -308,12 +308,15 @@ struct Ar<double> {
     return D > eps ? q / D : 0.0;
   }
   // Outflow limit: |flux| <= D dx / (4 dt) with D the depth of the cell it drains, and
-  // the velocity limit |flux| <= vlim Df (vlim = +inf when off, which leaves the cap).
+  // with the velocity limit (kernel variant kLim) also |flux| <= vlim Df.
+  template <bool kLim>
   static __device__ __forceinline__ double limit(double m, double Dlo, double Dhi, double Df,
                                                  const MomK<double>& K) {
     double cap = (m > 0.0 ? Dlo : Dhi) * K.dx / K.q4dt;
-    const double vc = K.vlim * Df;
-    if (vc < cap) cap = vc;
+    if (kLim) {
+      const double vc = K.vlim * Df;
+      if (vc < cap) cap = vc;
+    }
     if (m > cap) return cap;
     if (m < -cap) return -cap;
     return m;
@@ -339,9 +342,11 @@ struct Ar<float> {
   static __device__ __forceinline__ float face_vel(float q, float D, float eps) {
     return D > eps ? __fdividef(q, D) : 0.0f;
   }
+  template <bool kLim>
   static __device__ __forceinline__ float limit(float m, float Dlo, float Dhi, float Df,
                                                 const MomK<float>& K) {
-    const float cap = fminf((m > 0.0f ? Dlo : Dhi) * K.dxq, K.vlim * Df);
+    float cap = (m > 0.0f ? Dlo : Dhi) * K.dxq;
+    if (kLim) cap = fminf(cap, K.vlim * Df);
     if (m > cap) return cap;  // (a NaN passes through, for the non-finite check)
     if (m < -cap) return -cap;
     return m;
@@ -514,7 +519,7 @@ __device__ __forceinline__ Raw<T> read_row(const RingSlot<T>& S, int lane) {
 // and RX of rows j-1, j, j+1 with their usable flags. Every case of the wet/dry rule is
 // evaluated and the result selected (the values are those of the case analysis: a
 // discarded case may produce a NaN that is never selected).
-template <class T>
+template <bool kLim, class T>
 __device__ __forceinline__ T xmom_r(T hL, T eL, T hR, T eR, T m, T nb, bool okm, T qm, T q0,
                                     bool okp, T qp, bool oks, T rs, T r0, bool okn, T rn,
                                     float nL, float nR, const MomK<T>& K) {
@@ -531,13 +536,13 @@ __device__ __forceinline__ T xmom_r(T hL, T eL, T hR, T eR, T m, T nb, bool okm,
   const T nf = (T)(nL > nR ? nL : nR);
   const T m1 = Ar<T>::update(m, nb, Df, grad, adv, nf, K);
   const bool keep = (both || oneL || oneR) && Df > eps && (both || (wL ? !(m1 < T(0)) : !(m1 > T(0))));
-  const T lim = Ar<T>::limit(m1, hL + eL, hR + eR, Df, K);
+  const T lim = Ar<T>::template limit<kLim>(m1, hL + eL, hR + eR, Df, K);
   return keep ? lim : T(0);
 }
 
 // R3 + R4 at y-face (c, j): cells S = (c, j-1), N = (c, j); SY of rows j-1, j, j+1 and
 // TY of faces c-1, c, c+1 with their usable flags (selects as in xmom_r).
-template <class T>
+template <bool kLim, class T>
 __device__ __forceinline__ T ymom_r(T hS, T eS, T hN, T eN, T v, T mb, bool okm, T sm, T s0,
                                     bool okp, T sp, bool okw, T tw, T t0, bool oke, T te,
                                     float nS, float nN, const MomK<T>& K) {
@@ -554,7 +559,7 @@ __device__ __forceinline__ T ymom_r(T hS, T eS, T hN, T eN, T v, T mb, bool okm,
   const T nf = (T)(nS > nN ? nS : nN);
   const T v1 = Ar<T>::update(v, mb, Df, grad, adv, nf, K);
   const bool keep = (both || oneS || oneN) && Df > eps && (both || (wS ? !(v1 < T(0)) : !(v1 > T(0))));
-  const T lim = Ar<T>::limit(v1, hS + eS, hN + eN, Df, K);
+  const T lim = Ar<T>::template limit<kLim>(v1, hS + eS, hN + eN, Df, K);
   return keep ? lim : T(0);
 }
 
@@ -565,7 +570,7 @@ template <class T>
 __device__ __forceinline__ T upwind_open(T w, T phim, T phi0, T phip) {
   return w > T(0) ? phi0 - phim : (w < T(0) ? phip - phi0 : T(0.5) * (phip - phim));
 }
-template <class T>
+template <bool kLim, class T>
 __device__ __forceinline__ T mom_open(T hA, T eA, T hB, T eB, T m, T across, T pm, T p0, T pp,
                                       T qm, T q0, T qp, float nA, float nB, const MomK<T>& K) {
   const T Df = T(0.5) * (hA + hB) + T(0.5) * (eA + eB);
@@ -575,7 +580,7 @@ __device__ __forceinline__ T mom_open(T hA, T eA, T hB, T eB, T m, T across, T p
   const T adv = K.dtdx * (a1 + a2);
   const T nf = (T)(nA > nB ? nA : nB);
   const T m1 = Ar<T>::update(m, across, Df, grad, adv, nf, K);
-  const T lim = Ar<T>::limit(m1, hA + eA, hB + eB, Df, K);
+  const T lim = Ar<T>::template limit<kLim>(m1, hA + eA, hB + eB, Df, K);
   return Df > K.eps ? lim : T(0);
 }
 
@@ -692,7 +697,7 @@ __device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<
 // Step strip td at chunk step s (one warp; ws holds the strip's staged descriptor, the
 // prepass has run). The budget slot of the strip receives sum(eta^{n+1}) and adds the
 // clip, outflow and ring terms.
-template <class T, bool kTrack>
+template <class T, bool kTrack, bool kLim>
 __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& ws, Tile td,
                                             int s) {
   constexpr int kRingD = RingD<T>::D;
@@ -857,19 +862,19 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
         const T qm = __shfl_up_sync(full, Z.QX, 1), qp = __shfl_down_sync(full, Z.QX, 1);
         const T tw = __shfl_up_sync(full, Z.TY, 1), te = __shfl_down_sync(full, Z.TY, 1);
         const float nmL = __shfl_up_sync(full, Z.nm, 1);
-        xm = mom_open(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, qm, Z.QX, qp, Y.RX, Z.RX, X.RX, nmL,
+        xm = mom_open<kLim>(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, qm, Z.QX, qp, Y.RX, Z.RX, X.RX, nmL,
                       Z.nm, K);
-        ym = mom_open(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.SY, Z.SY, X.SY, tw, Z.TY, te, Y.nm,
+        ym = mom_open<kLim>(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, Y.SY, Z.SY, X.SY, tw, Z.TY, te, Y.nm,
                       Z.nm, K);
       } else if (__any_sync(full, act)) {
         const T qm = __shfl_up_sync(full, Z.QX, 1), qp = __shfl_down_sync(full, Z.QX, 1);
         const T tw = __shfl_up_sync(full, Z.TY, 1), te = __shfl_down_sync(full, Z.TY, 1);
         const float nmL = __shfl_up_sync(full, Z.nm, 1);
         const unsigned bx = __ballot_sync(full, Z.fl & 1u), by = __ballot_sync(full, Z.fl & 2u);
-        xm = xmom_r(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, ((bx >> sl) & 1u) != 0, qm, Z.QX,
+        xm = xmom_r<kLim>(Z.hL, Z.eL, Z.H, Z.E, Z.MX, Z.nb, ((bx >> sl) & 1u) != 0, qm, Z.QX,
                     ((bx >> sr) & 1u) != 0, qp, (Y.fl & 1u) != 0, Y.RX, Z.RX, (X.fl & 1u) != 0,
                     X.RX, nmL, Z.nm, K);
-        ym = ymom_r(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, (Y.fl & 2u) != 0, Y.SY, Z.SY,
+        ym = ymom_r<kLim>(Y.H, Y.E, Z.H, Z.E, Z.NY, Z.mb, (Y.fl & 2u) != 0, Y.SY, Z.SY,
                     (X.fl & 2u) != 0, X.SY, ((by >> sl) & 1u) != 0, tw, Z.TY,
                     ((by >> sr) & 1u) != 0, te, Y.nm, Z.nm, K);
       }
@@ -987,7 +992,9 @@ __device__ __forceinline__ bool grid_barrier(Bar* bar, unsigned& gen, int* statu
 // that keep the maximum velocity take the tracking march; kStepFeedback (cooperative
 // only), which also runs the full-feedback phase of each step, behind one more barrier.
 // A group with full feedback stepped one launch per step runs k_feedback before each
-// kStepPlain or kStepTrack launch instead.
+// kStepPlain or kStepTrack launch instead. The flag kStepLimit added to a variant
+// compiles in the velocity limit (a block without it has vlim = +inf, so its fluxes are
+// unchanged); groups without the limit run variants that do not evaluate it at all.
 // Resident CTAs per SM the register allocation targets: binary32 fits 96 registers
 // (5 CTAs of 4 warps) without spilling; binary64 keeps the compiler's choice.
 template <class T>
@@ -1054,18 +1061,20 @@ __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
 template <class T, int kMode>
 __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
     k_step(KParams<T> kp, int s_first, int s_count) {
-  constexpr bool kAnyTrack = kMode != kStepPlain;
+  constexpr int kBase = kMode & ~kStepLimit;
+  constexpr bool kLim = (kMode & kStepLimit) != 0;  // some block keeps the velocity limit
+  constexpr bool kAnyTrack = kBase != kStepPlain;
   __shared__ WarpSlot<T> slots[kWarps];
   __shared__ int go;
   WarpSlot<T>& ws = slots[threadIdx.y];
   if (threadIdx.x == 0) ws.blk = -1;
   __syncwarp();
   unsigned gen = 0;
-  if ((kMode == kStepFeedback || s_count > 1) && threadIdx.x == 0 && threadIdx.y == 0)
+  if ((kBase == kStepFeedback || s_count > 1) && threadIdx.x == 0 && threadIdx.y == 0)
     gen = ld_acquire_u32(&kp.bar->gen);
   const int nt = *kp.ntiles;
   for (int s = s_first; s < s_first + s_count; ++s) {
-    if (kMode == kStepFeedback) {  // full feedback, then a device-wide barrier
+    if (kBase == kStepFeedback) {  // full feedback, then a device-wide barrier
       feedback_items(kp, ws, s, blockIdx.x * kWarps + threadIdx.y, gridDim.x * kWarps);
       if (!grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go)) return;
     }
@@ -1081,8 +1090,8 @@ __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
       if ((long long)s >= ws.sc.remaining) continue;  // the scenario has finished
       if ((td.flags & kTfRing) || ws.b.is_child)
         strip_prepass(kp, ws, td, (int)((ws.sc.base + s) & 1));
-      if (kAnyTrack && ws.b.vmax) march_strip<T, true>(kp, ws, td, s);  // velocity tracked
-      else march_strip<T, false>(kp, ws, td, s);
+      if (kAnyTrack && ws.b.vmax) march_strip<T, true, kLim>(kp, ws, td, s);  // velocity tracked
+      else march_strip<T, false, kLim>(kp, ws, td, s);
     }
     if (s + 1 < s_first + s_count &&
         !grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go))

@@ -67,6 +67,8 @@ struct Blk {
 constexpr int kStepPlain = 0;     // no block keeps the maximum velocity
 constexpr int kStepTrack = 1;     // some block keeps it
 constexpr int kStepFeedback = 2;  // + the full-feedback phase (cooperative launch)
+constexpr int kStepLimit = 4;     // flag added to a variant: some block keeps the velocity limit
+constexpr int kStepModes = 8;     // mode values 0 .. 7 (3 and 7 unused)
 
 // nesting options of a block (Blk::nest)
 constexpr int kNestFull = 1;   // fine-to-coarse feedback on every covered parent cell
@@ -108,6 +110,7 @@ struct KParams {
   Bar* bar;
   int nsteps;
   int track;           // some block keeps the maximum velocity (selects the kernel variant)
+  int limit;           // some block keeps the velocity limit (selects the kernel variant)
   int tx, ty;          // tile shape in cells
   long long spin_cycles;
 #ifdef RTI_CHECKED

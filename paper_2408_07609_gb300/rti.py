@@ -78,6 +78,8 @@ def lib():
             "rti_set_initial_uplift": (C.c_int, [_vp, C.c_int, _dp]),
             "rti_step": (C.c_int, [_vp, C.c_int, _vp]),
             "rti_sync": (C.c_int, [_vp]),
+            "rti_sync_timeout": (C.c_int, [_vp, C.c_double]),
+            "rti_batch_sync_timeout": (C.c_int, [_vp, C.c_double]),
             "rti_get_max_depth": (C.c_int, [_vp, C.c_int, _dp]),
             "rti_get_max_height": (C.c_int, [_vp, C.c_int, _dp]),
             "rti_get_arrival_time": (C.c_int, [_vp, C.c_int, _dp]),
@@ -85,6 +87,9 @@ def lib():
             "rti_get_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
             "rti_set_state": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
             "rti_get_budget": (C.c_int, [_vp, C.c_int, _dp]),
+            "rti_checkpoint_bytes": (C.c_size_t, [_vp]),
+            "rti_checkpoint_save": (C.c_int, [_vp, _vp, C.c_size_t]),
+            "rti_checkpoint_load": (C.c_int, [_vp, _vp, C.c_size_t]),
             "rti_volume": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
             "rti_get_transfer_bytes": (C.c_int, [_vp, C.POINTER(C.c_longlong),
                                                  C.POINTER(C.c_longlong)]),
@@ -210,8 +215,12 @@ class Handle:
     def step(self, n=1, stream=None):
         self._chk(lib().rti_step(self._h, int(n), _stream_ptr(stream)), "step")
 
-    def sync(self):
-        self._chk(lib().rti_sync(self._h), "sync")
+    def sync(self, timeout=None):
+        """Wait for the enqueued work (at most `timeout` seconds: RtiError TIMEOUT after)."""
+        if timeout is None:
+            self._chk(lib().rti_sync(self._h), "sync")
+        else:
+            self._chk(lib().rti_sync_timeout(self._h, float(timeout)), "sync_timeout")
 
     def get_state(self, k):
         ny, nx = self.shape(k)
@@ -254,6 +263,18 @@ class Handle:
         out = np.empty(4)
         self._chk(lib().rti_get_budget(self._h, k, out.ctypes.data_as(_dp)), "budget")
         return dict(volume=out[0], outflow=out[1], clip=out[2], ring=out[3])
+
+    def checkpoint(self) -> bytes:
+        """The whole handle's state as bytes (rti_checkpoint_save)."""
+        n = lib().rti_checkpoint_bytes(self._h)
+        buf = C.create_string_buffer(n)
+        self._chk(lib().rti_checkpoint_save(self._h, buf, n), "checkpoint_save")
+        return buf.raw
+
+    def restore(self, data: bytes):
+        """Resume from a checkpoint of a handle with the same blocks and params."""
+        buf = C.create_string_buffer(data, len(data))
+        self._chk(lib().rti_checkpoint_load(self._h, buf, len(data)), "checkpoint_load")
 
     def volume(self):
         """Whole-domain budget over the root blocks (rti_volume)."""
@@ -321,8 +342,9 @@ class Batch:
     def remaining(self, h: Handle) -> int:
         return lib().rti_batch_remaining(self._b, h._h)
 
-    def sync(self):
-        rc = lib().rti_batch_sync(self._b)
+    def sync(self, timeout=None):
+        rc = (lib().rti_batch_sync(self._b) if timeout is None
+              else lib().rti_batch_sync_timeout(self._b, float(timeout)))
         if rc:
             raise RtiError(rc, "rti_batch_sync")
 
