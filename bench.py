@@ -42,7 +42,7 @@ BYTES_PER_CELL_STEP = {"f32": 5 * 4 + 4 + 3 * 4,   # 36
 # cell-steps of FP64 oracle work per host thread the reference arm spreads over its W + K
 # steps (about a minute)
 REF_CELL_STEPS = 0.8e9
-NCU_F32_DRAM_BYTES_PER_CELL_STEP = (229.652992e6 + 83.252480e6) / 7.95e6  # 39.4 B
+NCU_F32_DRAM_BYTES_PER_CELL_STEP = (229.257472e6 + 83.613952e6) / 7.95e6  # 39.35 B
 
 
 def parse():

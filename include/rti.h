@@ -102,7 +102,9 @@ typedef struct rti_handle rti_handle;
 typedef struct rti_batch rti_batch;
 
 /* Device bytes rti_create needs for this hierarchy (the arena size for a caller-owned
- * arena). Validates the descriptors like rti_create but reads no bathymetry. */
+ * arena): the planes of every block of the nested grid system (Sec. II-A, Fig. 1's levels
+ * and blocks) in the state precision. Validates the descriptors like rti_create (the
+ * 1:3 inclusive nesting of Sec. II-A) but reads no bathymetry. */
 int rti_footprint(const rti_block* blocks, int nblocks, const rti_params* params, size_t* bytes);
 
 /* Build a hierarchy on the current CUDA device. bathy[b] (nx*ny doubles) and manning[b]
@@ -121,8 +123,11 @@ int rti_create(const rti_block* blocks, int nblocks, const double* const* bathy,
 int rti_set_initial_uplift(rti_handle* h, int block, const double* dz);
 
 /* Enqueue nsteps time steps of the whole hierarchy on `stream` (a cudaStream_t, NULL =
- * the legacy default stream) and return without waiting. Device errors (non-finite
- * level, barrier timeout) are reported by the next call that waits. */
+ * the legacy default stream) and return without waiting. One step is the time-integration
+ * loop body of Sec. IV-A / Fig. 2 on every block with one dt (Sec. V-A): mass (Eq. 1),
+ * fine-to-coarse level (Sec. IV-C-2, Listing 5), momentum (Eqs. 2-3), coarse-to-fine
+ * fluxes, output update, buffer swap. Device errors (non-finite level, barrier timeout)
+ * are reported by the next call that waits. */
 int rti_step(rti_handle* h, int nsteps, void* stream);
 
 /* Wait for the handle's enqueued work and return its device status. */
@@ -148,8 +153,11 @@ int rti_get_arrival_time(rti_handle* h, int block, double* out);
  * Needs track_velocity = 1 at create; otherwise RTI_ERR_STATE. */
 int rti_get_max_velocity(rti_handle* h, int block, double* out);
 
-/* Checkpoint access: current eta (nx*ny), M (ny*(nx+1)), N ((ny+1)*nx); NULL skips one.
- * rti_set_state leaves maxima, arrival, budget terms and the step counter unchanged. */
+/* State access: current eta (nx*ny), M (ny*(nx+1)), N ((ny+1)*nx) of one block, the
+ * variables of Eqs. 1-3 on the staggered grid (eta at cell centres, M and N on the x and
+ * y faces), in binary64; a child's edge fluxes are those the next step takes from its
+ * parent. NULL skips one. rti_set_state leaves maxima, arrival, budget terms and the step
+ * counter unchanged. */
 int rti_get_state(rti_handle* h, int block, double* eta, double* M, double* N);
 int rti_set_state(rti_handle* h, int block, const double* eta, const double* M,
                   const double* N);
@@ -245,9 +253,13 @@ int rti_step_noalloc(const rti_block* grid, const rti_params* params,
                      void* stream);
 
 /* ---- Batches: many hierarchies stepped together in one persistent launch ----
- * All handles of a batch share one precision. A handle in a batch is stepped only by
- * rti_batch_step (rti_step returns RTI_ERR_STATE). Adding or removing members patches
- * the device-resident tile list; the captured CUDA graph is reused. */
+ * The paper steps one hierarchy per run (Sec. IV-A) and launches a kernel per block on
+ * asynchronous queues (Sec. IV-B); a batch steps the blocks of many independent
+ * hierarchies (earthquake scenarios) through the same loop body in one launch, each
+ * hierarchy exactly as rti_step would. All handles of a batch share one precision. A
+ * handle in a batch is stepped only by rti_batch_step (rti_step returns RTI_ERR_STATE).
+ * Adding or removing members patches the device-resident tile list; the captured CUDA
+ * graph is reused. */
 int rti_batch_create(int precision, int schedule, int chunk_steps, rti_batch** out);
 /* The same with the strip height and CTA cap of the batch (members must be created with
  * the same tile_y); rti_batch_create uses tile_y 64 and no cap. */

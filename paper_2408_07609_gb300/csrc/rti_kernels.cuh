@@ -580,8 +580,9 @@ __device__ __forceinline__ T mom_open(T hA, T eA, T hB, T eB, T m, T across, T p
   const T adv = K.dtdx * (a1 + a2);
   const T nf = (T)(nA > nB ? nA : nB);
   const T m1 = Ar<T>::update(m, across, Df, grad, adv, nf, K);
-  const T lim = Ar<T>::template limit<kLim>(m1, hA + eA, hB + eB, Df, K);
-  return Df > K.eps ? lim : T(0);
+  // no Df > eps test: the open-water vote requires both faces of the update usable
+  // (depth above dry_eps) on every lane whose result is stored
+  return Ar<T>::template limit<kLim>(m1, hA + eA, hB + eB, Df, K);
 }
 
 // R6: flux leaving through a root edge next to a cell (sign +1 east/north, -1 west/south)
@@ -1008,13 +1009,21 @@ struct StepOcc<float> {
 
 // Full-feedback items of step s (R8 on every covered parent cell): items t = w, w + nw,
 // ... of warp w of nw. An item is parent row J, parent cells I0 .. I0 + 31 of one child's
-// footprint; each lane forms the mean of one parent cell from the child's eta^{n+1}
-// recomputed from its level p, into the parent's ring plane, which the parent's strips
-// read once the phase has ended. The descriptors go through the warp's slot (parent in
-// ws.b, child in ws.P), which the strip phase stages again.
+// footprint: the child's eta^{n+1} on its 3 rows x 96 columns below them, recomputed from
+// its level p with the lanes on consecutive child columns (coalesced loads), go through
+// the warp's ring memory (free in this phase) with their wet flags; then lane k forms
+// the mean of parent cell I0 + k from its 3x3 patch there (binary64, Listing 5 order:
+// x outer, y inner), into the parent's ring plane, which the parent's strips read once
+// the phase has ended. The descriptors go through the warp's slot (parent in ws.b,
+// child in ws.P), which the strip phase stages again.
 template <class T>
 __device__ __noinline__ void feedback_items(const KParams<T>& kp, WarpSlot<T>& ws, int s,
                                             int w, int nw) {
+  constexpr double kInvWet[10] = {0.0,       1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0,
+                                  1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0};
+  static_assert(sizeof(ws.ring) >= 3 * 96 * (sizeof(T) + 1), "feedback scratch");
+  T* ev = reinterpret_cast<T*>(&ws.ring[0]);                              // [3][96]
+  unsigned char* wf = reinterpret_cast<unsigned char*>(ev + 3 * 96);      // [3][96]
   const int n = *kp.nfb;
   const int lane = threadIdx.x;
   int have_p = -1, have_c = -1;
@@ -1036,13 +1045,37 @@ __device__ __noinline__ void feedback_items(const KParams<T>& kp, WarpSlot<T>& w
     const ScenDev sc = kp.scen[P.scen];
     if ((long long)s >= sc.remaining) continue;  // the scenario has finished
     const int p = (int)((sc.base + s) & 1);
-    const int I = it.I0 + lane;
-    if (I < c.i0 + c.nx / 3) {
-      const size_t o = ix(P, I, it.J);
-      T rv;
-      const bool wet = ring_patch(c, P, p, I - c.i0, it.J - c.j0, P.h[o], rv);
-      P.ring[o] = wet ? rv : ring_none(rv);
+    const int ncell = min(32, c.i0 + c.nx / 3 - it.I0);  // parent cells of this item
+    const int x0 = 3 * (it.I0 - c.i0), y0 = 3 * (it.J - c.j0);
+    for (int k = lane; k < 3 * 3 * ncell; k += 32) {  // row-major over 3 rows x 3 ncell cols
+      const int yy = k / (3 * ncell), xx = k - yy * 3 * ncell;
+      const T e = child_eta_next(c, P, p, x0 + xx, y0 + yy);
+      ev[yy * 96 + xx] = e;
+      wf[yy * 96 + xx] = c.h[ix(c, x0 + xx, y0 + yy)] + e > c.eps;
     }
+    __syncwarp();
+    if (lane < ncell) {
+      double sum = 0.0;
+      int wet = 0;
+      for (int x = 3 * lane; x < 3 * lane + 3; ++x) {  // outer: x (the paper's J)
+        for (int y = 0; y < 3; ++y) {                  // inner: y (the paper's I)
+          if (wf[y * 96 + x]) {
+            sum = sum + (double)ev[y * 96 + x];
+            wet = wet + 1;
+          }
+        }
+      }
+      const size_t o = ix(P, it.I0 + lane, it.J);
+      if (wet == 0) {
+        P.ring[o] = ring_none(T(0));
+      } else {
+        double avg = sum * kInvWet[wet];
+        const double hP = (double)P.h[o];
+        if (avg < -hP) avg = -hP;
+        P.ring[o] = (T)avg;
+      }
+    }
+    __syncwarp();
   }
   __syncwarp();
   if (lane == 0) ws.blk = -1;  // the slot no longer holds a strip's descriptors
