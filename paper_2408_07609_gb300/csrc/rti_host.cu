@@ -12,6 +12,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <queue>
 #include <string>
 #include <thread>
 #include <vector>
@@ -177,10 +178,9 @@ struct Group {
   size_t cap_kids = 0;
   Tile* d_tiles = nullptr;
   size_t cap_tiles = 0;
-  int* d_counts = nullptr;  // [0] = ntiles, [1] = nscen, [2] = full-feedback items
-  FbItem* d_fb = nullptr;
-  size_t cap_fb = 0;
-  int nfb = 0;
+  int* d_counts = nullptr;  // [0] = ntiles, [1] = nscen
+  unsigned long long* d_done = nullptr;  // per strip: progress flag (full feedback)
+  size_t cap_done = 0;      // bytes
   ScenDev* d_scen = nullptr;
   size_t cap_scen = 0;
   int* d_status = nullptr;
@@ -190,6 +190,7 @@ struct Group {
   int cap = 0;                   // CTAs per SM cap (0 = none)
   bool track = false;            // some member keeps the maximum velocity
   bool limit = false;            // some member keeps the velocity limit
+  bool full = false;             // some member has full feedback (finer levels listed first)
   long long spin_cycles = kSpinCycles;
   // pinned staging for table uploads
   char* h_stage = nullptr;
@@ -306,7 +307,7 @@ void free_group_dev(Group* g) {
   cudaFree(g->d_kids);
   cudaFree(g->d_tiles);
   cudaFree(g->d_counts);
-  cudaFree(g->d_fb);
+  cudaFree(g->d_done);
   cudaFree(g->d_scen);
   cudaFree(g->d_status);
   cudaFree(g->d_bar);
@@ -317,7 +318,7 @@ void free_group_dev(Group* g) {
   g->d_kids = nullptr;
   g->d_tiles = nullptr;
   g->d_counts = nullptr;
-  g->d_fb = nullptr;
+  g->d_done = nullptr;
   g->d_scen = nullptr;
   g->d_status = nullptr;
   g->d_bar = nullptr;
@@ -333,10 +334,10 @@ int group_init(Group* g, int prec, int sched, int tx, int ty, int chunk, int cap
   g->tx = tx;
   g->ty = ty;
   g->chunk = chunk;
-  cudaError_t e = cudaMalloc(&g->d_counts, 3 * sizeof(int));
+  cudaError_t e = cudaMalloc(&g->d_counts, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_bar, sizeof(Bar));
-  if (e == cudaSuccess) e = cudaMemset(g->d_counts, 0, 3 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->d_counts, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->d_bar, 0, sizeof(Bar));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->staged, cudaEventDisableTiming);
@@ -360,15 +361,15 @@ KParams<T> kparams(Group* g, int nsteps) {
   kp.kids = g->d_kids;
   kp.tiles = g->d_tiles;
   kp.ntiles = g->d_counts;
-  kp.fb = g->d_fb;
-  kp.nfb = g->d_counts + 2;
-  kp.fb_any = g->nfb > 0 ? 1 : 0;
+  kp.done = g->d_done;
+  kp.ndone = (int)(g->cap_done / sizeof(*g->d_done));
   kp.scen = g->d_scen;
   kp.status = g->d_status;
   kp.bar = g->d_bar;
   kp.nsteps = nsteps;
   kp.track = g->track ? 1 : 0;
   kp.limit = g->limit ? 1 : 0;
+  kp.full = g->full ? 1 : 0;
   kp.tx = g->tx;
   kp.ty = g->ty;
   kp.spin_cycles = g->spin_cycles;
@@ -394,19 +395,110 @@ cudaError_t grow(T** ptr, size_t* cap, size_t need_bytes, bool* moved) {
   return e;
 }
 
+// Order of the work list of a group with full feedback (list scheduling on the critical
+// path). A parent's ring strip with full feedback waits for the child strips that own
+// the patches under its region (the ranges the kernel waits for, strip_prepass). Each
+// strip weighs its cells, a ring strip 1.3 times (it also reads the ring plane); its rank
+// is its weight plus the largest rank among the strips that wait for it, i.e. the
+// longest chain of waits it starts. A simulation of `workers` warps, each taking, as it
+// frees up, the highest-ranked strip whose dependencies have ended, gives the handout
+// order: deep chains start first, the rest fills in around them, and every strip comes
+// after the strips it waits for (so a waiting warp waits only on strips already handed
+// out). `tiles` holds each block's strips from index strip0 on, row by row.
+template <class T>
+std::vector<Tile> full_feedback_order(const std::vector<Blk<T>>& blks,
+                                      const std::vector<int>& kids,
+                                      const std::vector<Tile>& tiles, int tx, int ty,
+                                      int workers) {
+  const int n = (int)tiles.size();
+  std::vector<double> w(n), rank(n);
+  std::vector<std::vector<int>> deps(n), users(n);
+  for (int t = 0; t < n; ++t) {
+    const Tile& td = tiles[t];
+    const Blk<T>& b = blks[td.blk];
+    const int cols = std::min(tx, b.nx - td.x0), rows = std::min(ty, b.ny - td.y0);
+    w[t] = (double)cols * rows * ((td.flags & kTfRing) ? 1.3 : 1.0);
+    if (!(td.flags & kTfRing) || !(b.nest & kNestFull)) continue;
+    const int ye = std::min(td.y0 + ty, b.ny);
+    const int c0 = std::max(td.x0 - 2, 0), c1 = std::min(td.x0 + tx + 2, b.nx);
+    const int r0 = std::max(td.y0 - 2, 0), r1 = std::min(ye + 1, b.ny);
+    for (int q = 0; q < b.child_count; ++q) {
+      const Blk<T>& c = blks[kids[b.child_first + q]];
+      const int a0 = c.i0, a1 = c.i0 + c.nx / 3, b0 = c.j0, b1 = c.j0 + c.ny / 3;
+      const int u0 = std::max(c0, a0) - a0, u1 = std::min(c1, a1) - a0;
+      const int v0 = std::max(r0, b0) - b0, v1 = std::min(r1, b1) - b0;
+      if (u0 >= u1 || v0 >= v1) continue;
+      for (int sy = (3 * v0 + 2) / ty; sy <= (3 * (v1 - 1) + 2) / ty; ++sy)
+        for (int sx = (3 * u0 + 2) / tx; sx <= (3 * (u1 - 1) + 2) / tx; ++sx)
+          deps[t].push_back(c.strip0 + sy * c.tiles_x + sx);
+    }
+    for (int d : deps[t]) users[d].push_back(t);
+  }
+  // ranks, coarse levels first (a strip's waiters sit one level up)
+  std::vector<int> level(blks.size(), 0);
+  for (size_t k = 0; k < blks.size(); ++k)
+    for (int a = blks[k].parent; a >= 0; a = blks[a].parent) ++level[k];
+  std::vector<int> by_level(n);
+  for (int t = 0; t < n; ++t) by_level[t] = t;
+  std::stable_sort(by_level.begin(), by_level.end(), [&](int a, int b) {
+    return level[tiles[a].blk] < level[tiles[b].blk];
+  });
+  for (int t : by_level) {
+    double up = 0.0;
+    for (int u : users[t]) up = std::max(up, rank[u]);
+    rank[t] = w[t] + up;
+  }
+  // the simulated handout
+  std::vector<int> left(n);
+  std::priority_queue<std::pair<double, int>> ready;  // (rank, -index): lowest index on ties
+  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>,
+                      std::greater<std::pair<double, int>>>
+      running;  // (finish time, index)
+  for (int t = 0; t < n; ++t) {
+    left[t] = (int)deps[t].size();
+    if (!left[t]) ready.push({rank[t], -t});
+  }
+  std::vector<Tile> out;
+  std::vector<char> taken(n, 0);
+  out.reserve(n);
+  double now = 0.0;
+  int idle = std::max(workers, 1);
+  while ((int)out.size() < n) {
+    while (idle > 0 && !ready.empty()) {
+      const int t = -ready.top().second;
+      ready.pop();
+      out.push_back(tiles[t]);
+      taken[t] = 1;
+      running.push({now + w[t], t});
+      --idle;
+    }
+    if (running.empty()) break;  // nothing left that can start (no dependency cycle exists)
+    const std::pair<double, int> f = running.top();
+    running.pop();
+    now = f.first;
+    ++idle;
+    for (int u : users[f.second])
+      if (--left[u] == 0) ready.push({rank[u], -u});
+  }
+  for (int t = 0; t < n; ++t)
+    if (!taken[t]) out.push_back(tiles[t]);
+  return out;
+}
+
 // Rebuild and upload the block table, child lists and tile list of a group (stream-ordered).
 template <class T>
 int group_upload(Group* g, cudaStream_t st, std::string* err) {
   std::vector<Blk<T>> blks;
   std::vector<int> kids;
   std::vector<Tile> tiles;
-  std::vector<FbItem> fb;
+  int nflags = 0;  // strips of the group (one flag each)
   long long cells = 0;
-  bool track = false, limit = false;
+  bool track = false, limit = false, full_any = false;
   for (size_t mi = 0; mi < g->members.size(); ++mi) {
     rti_handle* h = g->members[mi];
     track = track || h->params.track_velocity != 0;
     limit = limit || h->params.velocity_limit > 0;
+    full_any = full_any || h->params.nest_feedback == RTI_NEST_FULL;
     const int base = (int)blks.size();
     const int nb = (int)h->blocks.size();
     std::vector<std::vector<int>> ch(nb);
@@ -416,15 +508,8 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
       const int cf = (int)kids.size();
       for (int c : ch[k]) kids.push_back(base + c);
       blks.push_back(make_blk<T>(h, k, base, (int)mi, cf, (int)ch[k].size(), g->tx));
-    }
-    if (h->params.nest_feedback == RTI_NEST_FULL) {  // every covered cell, 32 per item
-      for (int c = 0; c < nb; ++c) {
-        const rti_block& cd = h->blocks[c];
-        if (cd.parent < 0) continue;
-        for (int J = cd.j0; J < cd.j0 + cd.ny / 3; ++J)
-          for (int I0 = cd.i0; I0 < cd.i0 + cd.nx / 3; I0 += 32)
-            fb.push_back(FbItem{base + cd.parent, base + c, J, I0});
-      }
+      blks.back().strip0 = nflags;
+      nflags += h->mem[k].tiles_x * h->mem[k].tiles_y;
     }
     for (int k = 0; k < nb; ++k) {
       const rti_block& d = h->blocks[k];
@@ -456,26 +541,38 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
       }
     }
   }
-  // strips with nesting work (a ring, or a child's edge) first: the step kernel hands
-  // strips out in list order, so the slow ones start early
-  std::stable_partition(tiles.begin(), tiles.end(), [&](const Tile& t) {
-    const Blk<T>& b = blks[t.blk];
-    const bool edge = b.is_child && (t.x0 == 0 || t.x0 + kStripW + 2 >= b.nx || t.y0 == 0 ||
-                                     t.y0 + g->ty + 2 >= b.ny);
-    return (t.flags & kTfRing) || edge;
-  });
+  // The step kernel hands strips out in list order. Strips with nesting work (a ring, or
+  // a child's edge) go first, so that the slow ones start early. With full feedback a
+  // parent's ring strip reads the means its children's strips formed this step and waits
+  // for the flags of the child strips under its region: the list then follows a
+  // simulated schedule (full_feedback_order) in which a strip comes after every strip it
+  // waits for, so that it waits only on running warps, which wait on nothing later in the
+  // list (no cycle).
+  if (!full_any) {
+    std::stable_partition(tiles.begin(), tiles.end(), [&](const Tile& t) {
+      const Blk<T>& b = blks[t.blk];
+      const bool edge = b.is_child && (t.x0 == 0 || t.x0 + g->tx + 2 >= b.nx || t.y0 == 0 ||
+                                       t.y0 + g->ty + 2 >= b.ny);
+      return (t.flags & kTfRing) || edge;
+    });
+  } else {
+    const int mode = (track ? kStepTrack : kStepPlain) | (limit ? kStepLimit : 0) | kStepFull;
+    int grid = 0;
+    if (persistent_grid<T>(&grid, g->tx, g->ty, mode, g->cap) != cudaSuccess || grid <= 0)
+      grid = g->grid;
+    tiles = full_feedback_order<T>(blks, kids, tiles, g->tx, g->ty, grid * kWarps);
+  }
   bool moved = false;
   cudaError_t e = grow(&g->d_blk, &g->cap_blk, blks.size() * sizeof(Blk<T>) + 64, &moved);
   if (e == cudaSuccess) e = grow(&g->d_kids, &g->cap_kids, kids.size() * sizeof(int) + 64, &moved);
   if (e == cudaSuccess) e = grow(&g->d_tiles, &g->cap_tiles, tiles.size() * sizeof(Tile) + 64, &moved);
   if (e == cudaSuccess)
     e = grow(&g->d_scen, &g->cap_scen, g->members.size() * sizeof(ScenDev) + 64, &moved);
-  if (e == cudaSuccess) e = grow(&g->d_fb, &g->cap_fb, fb.size() * sizeof(FbItem) + 64, &moved);
+  if (e == cudaSuccess)
+    e = grow(&g->d_done, &g->cap_done, (size_t)nflags * sizeof(*g->d_done), &moved);
   if (e != cudaSuccess) return cuda_err(err, e, "device tables");
-  // the captured graph holds the old pointers, the other kernel variant, or launches
-  // with or without the feedback phase
-  if ((moved || track != g->track || limit != g->limit || fb.empty() != (g->nfb == 0)) &&
-      g->gexec) {
+  // the captured graph holds the old pointers and sizes, or the other kernel variant
+  if ((moved || track != g->track || limit != g->limit || full_any != g->full) && g->gexec) {
     cudaGraphExecDestroy(g->gexec);
     g->gexec = nullptr;
     g->graph_tried = false;
@@ -484,9 +581,8 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   const size_t nb_kids = kids.size() * sizeof(int);
   const size_t nb_tiles = tiles.size() * sizeof(Tile);
   const size_t nb_scen = g->members.size() * sizeof(ScenDev);
-  const size_t nb_fb = fb.size() * sizeof(FbItem);
   const size_t need = align256(nb_blk) + align256(nb_kids) + align256(nb_tiles) +
-                      align256(nb_scen) + align256(nb_fb) + 256;
+                      align256(nb_scen) + 256;
   // the previous upload must have left the staging buffer before it is rewritten
   e = cudaEventSynchronize(g->staged);
   if (e != cudaSuccess) return cuda_err(err, e, "staging wait");
@@ -511,12 +607,11 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
     sc[mi].base = g->members[mi]->base;
     sc[mi].remaining = g->remaining[mi];
   }
-  int counts[3] = {(int)tiles.size(), (int)g->members.size(), (int)fb.size()};
+  int counts[2] = {(int)tiles.size(), (int)g->members.size()};
   e = put(blks.data(), nb_blk, g->d_blk);
   if (e == cudaSuccess) e = put(kids.data(), nb_kids, g->d_kids);
   if (e == cudaSuccess) e = put(tiles.data(), nb_tiles, g->d_tiles);
   if (e == cudaSuccess) e = put(sc.data(), nb_scen, g->d_scen);
-  if (e == cudaSuccess) e = put(fb.data(), nb_fb, g->d_fb);
   if (e == cudaSuccess) e = put(counts, sizeof(counts), g->d_counts);
   if (e == cudaSuccess) e = cudaEventRecord(g->staged, st);
   if (e != cudaSuccess) return cuda_err(err, e, "table upload");
@@ -526,7 +621,7 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   g->cells = cells;
   g->track = track;
   g->limit = limit;
-  g->nfb = (int)fb.size();
+  g->full = full_any;
   g->dirty = false;
   return RTI_OK;
 }
@@ -535,13 +630,10 @@ int group_upload_any(Group* g, cudaStream_t st, std::string* err) {
   return g->prec == RTI_FP32 ? group_upload<float>(g, st, err) : group_upload<double>(g, st, err);
 }
 
-// grid of the variant a chunk of this group launches (the smallest of the variants a
-// one-launch-per-step chunk uses), computed on first use
+// grid of the variant a chunk of this group launches, computed on first use
 int launch_grid(Group* g) {
-  const int lim = g->limit ? kStepLimit : 0;
-  const int mode = (g->sched == RTI_SCHED_PERSISTENT && g->nfb > 0
-                        ? kStepFeedback
-                        : (g->track ? kStepTrack : kStepPlain)) | lim;
+  const int mode = (g->track ? kStepTrack : kStepPlain) | (g->limit ? kStepLimit : 0) |
+                   (g->full ? kStepFull : 0);
   if (!g->grids[mode]) {
     int grid = 0;
     const cudaError_t e =
@@ -1560,6 +1652,7 @@ struct NoAllocScratch {
   ScenDev scen;
   Bar bar;
   int kids[4];
+  unsigned long long done[4];  // strip flags of full feedback (unused by a lone root)
   Tile tiles[kNoAllocMaxTiles];
   double budget[4 * kNoAllocMaxTiles];
 };
@@ -1659,6 +1752,8 @@ int noalloc_run(NoAllocScratch* s, const rti_block* g, const rti_params* p,
     kp.scen = &s->scen;
     kp.status = &s->status_group;
     kp.bar = &s->bar;
+    kp.done = s->done;
+    kp.ndone = 1;
     kp.nsteps = nsteps;
     kp.tx = tx;
     kp.ty = ty;

@@ -5,16 +5,19 @@
 namespace rti {
 
 namespace {
-// the step kernel of variant `mode` (kStep* base, plus kStepLimit); null for an unused mode
+// the step kernel of variant `mode` (kStepPlain or kStepTrack, plus kStepLimit and
+// kStepFull)
 using StepFn = void (*)(KParams<RTI_T>, int, int);
 StepFn step_kernel(int mode) {
   switch (mode) {
-    case kStepPlain: return k_step<RTI_T, kStepPlain>;
-    case kStepTrack: return k_step<RTI_T, kStepTrack>;
-    case kStepFeedback: return k_step<RTI_T, kStepFeedback>;
-    case kStepPlain | kStepLimit: return k_step<RTI_T, kStepPlain | kStepLimit>;
-    case kStepTrack | kStepLimit: return k_step<RTI_T, kStepTrack | kStepLimit>;
-    case kStepFeedback | kStepLimit: return k_step<RTI_T, kStepFeedback | kStepLimit>;
+    case 0: return k_step<RTI_T, 0>;
+    case 1: return k_step<RTI_T, 1>;
+    case 2: return k_step<RTI_T, 2>;
+    case 3: return k_step<RTI_T, 3>;
+    case 4: return k_step<RTI_T, 4>;
+    case 5: return k_step<RTI_T, 5>;
+    case 6: return k_step<RTI_T, 6>;
+    case 7: return k_step<RTI_T, 7>;
     default: return nullptr;
   }
 }
@@ -39,8 +42,11 @@ template <>
 cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid,
                                 const int* nscen, cudaStream_t st) {
   const dim3 blk(32, kWarps);
-  const int lim = kp.limit ? kStepLimit : 0;
+  const int mode = (kp.track ? kStepTrack : kStepPlain) | (kp.limit ? kStepLimit : 0) |
+                   (kp.full ? kStepFull : 0);
   cudaError_t e = cudaMemsetAsync(kp.bar, 0, sizeof(Bar), st);  // barrier and strip counters
+  if (e == cudaSuccess && kp.full)  // the strip flags of full feedback
+    e = cudaMemsetAsync(kp.done, 0, (size_t)kp.ndone * sizeof(*kp.done), st);
   if (e != cudaSuccess) return e;
   if (schedule == 0) {  // one cooperative launch for the whole chunk
     cudaLaunchConfig_t cfg = {};
@@ -53,12 +59,10 @@ cudaError_t launch_chunk<RTI_T>(const KParams<RTI_T>& kp, int schedule, int grid
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const int mode = (kp.fb_any ? kStepFeedback : kp.track ? kStepTrack : kStepPlain) | lim;
     e = cudaLaunchKernelEx(&cfg, step_kernel(mode), kp, 0, kp.nsteps);
-  } else {  // one launch per step (and one for the full-feedback phase before it)
-    const StepFn fn = step_kernel((kp.track ? kStepTrack : kStepPlain) | lim);
+  } else {  // one launch per step
+    const StepFn fn = step_kernel(mode);
     for (int s = 0; s < kp.nsteps && e == cudaSuccess; ++s) {
-      if (kp.fb_any) k_feedback<RTI_T><<<grid, blk, 0, st>>>(kp, s);
       fn<<<grid, blk, 0, st>>>(kp, s, 1);
       e = cudaGetLastError();
     }

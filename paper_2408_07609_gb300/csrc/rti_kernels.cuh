@@ -398,6 +398,7 @@ struct Raw {
   float nm;
   T vm;      // squared-speed maximum (velocity tracking only)
   T eN, hN;  // eta^n and h of cell (c, r + 1) (velocity tracking only)
+  T rv;      // ring-plane entry of cell (c, r) (ring strips only)
 };
 
 // The march's input rows are staged ahead in shared memory: a ring of kRingD slots per
@@ -418,11 +419,18 @@ struct RingD<double> {
 };
 constexpr int kRingW = 36;
 
-template <class T>
+template <class T, bool kRg>
 struct __align__(16) RingSlot {
   T e[kRingW], h[kRingW], m[kRingW], nn[kRingW], em[kRingW];
   float nm[kRingW];
   T vm[kRingW];  // squared-speed maximum, staged only when the block tracks it
+  T rg[kRingW];  // ring-plane entries (ring strips of full-feedback variants)
+};
+template <class T>
+struct __align__(16) RingSlot<T, false> {  // the other variants read the ring plane directly
+  T e[kRingW], h[kRingW], m[kRingW], nn[kRingW], em[kRingW];
+  float nm[kRingW];
+  T vm[kRingW];
 };
 
 // One 16-byte copy, issued only where `issue` holds (a predicate on the instruction, not
@@ -486,13 +494,14 @@ __device__ __forceinline__ void cp_async16x5(bool issue, unsigned d, const void*
       : "memory");
 }
 
-template <class T, bool kTrack>
-__device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T* h, const T* M,
+template <class T, bool kTrack, bool kRg>
+__device__ __forceinline__ void stage_row(RingSlot<T, kRg>& S, const T* eta, const T* h, const T* M,
                                           const T* N, const T* emax, const float* man,
-                                          const T* vmax, int rowbase, int pitch,
+                                          const T* vmax, const T* ring, int rowbase, int pitch,
                                           const StageLane& L, bool row_ok) {
-  static_assert(offsetof(RingSlot<T>, h) == kRingW * sizeof(T) &&
-                    offsetof(RingSlot<T>, em) == 4 * kRingW * sizeof(T),
+  using Slot = RingSlot<T, kRg>;
+  static_assert(offsetof(Slot, h) == kRingW * sizeof(T) &&
+                    offsetof(Slot, em) == 4 * kRingW * sizeof(T),
                 "state rows kRingW elements apart");
   const int g = L.oe ? rowbase + L.ke : rowbase;
   cp_async16x5<kRingW * (int)sizeof(T)>(row_ok && L.ie,
@@ -500,10 +509,13 @@ __device__ __forceinline__ void stage_row(RingSlot<T>& S, const T* eta, const T*
                                         h + g, M + g, N + g + pitch, emax + g, L.oe);
   cp_async16(row_ok && L.im, &S.nm[L.km], man + (L.om ? rowbase + L.km : rowbase), L.om);
   if (kTrack) cp_async16(row_ok && L.ie, &S.vm[L.ke], vmax + g, L.oe);
+  if constexpr (kRg) {
+    if (ring) cp_async16(row_ok && L.ie, &S.rg[L.ke], ring + g, L.oe);
+  }
 }
 
-template <class T, bool kTrack>
-__device__ __forceinline__ Raw<T> read_row(const RingSlot<T>& S, int lane) {
+template <class T, bool kTrack, bool kRg>
+__device__ __forceinline__ Raw<T> read_row(const RingSlot<T, kRg>& S, int lane) {
   Raw<T> R;
   R.e = S.e[lane + 2];
   R.h = S.h[lane + 2];
@@ -592,11 +604,22 @@ __device__ __forceinline__ T radiate_r(T h, T e, T sign, T eps, T g) {
   return sign * (dsqrt(g * (h > T(0) ? h : T(0))) * e);
 }
 
-// Per-warp shared memory: the strip's block descriptor (and its parent's), its
-// scenario counters and the index of the block staged.
-template <class T>
+// Per-warp shared memory: the input ring, the strip's block descriptor (and its
+// parent's), its scenario counters and the index of the block staged. The variants with
+// full feedback (kFull) also stage the ring plane and keep the rows the patch means need;
+// the others do without that shared memory (a larger footprint costs them L1 capacity).
+template <class T, bool kFull>
 struct WarpSlot {
-  RingSlot<T> ring[RingD<T>::D];
+  RingSlot<T, kFull> ring[RingD<T>::D];
+  Blk<T> b;
+  Blk<T> P;
+  ScenDev sc;
+  int blk;
+  T fb[3][32];  // eta^{n+1} before the ring override, rows r mod 3 (kFull only)
+};
+template <class T>
+struct WarpSlot<T, false> {
+  RingSlot<T, false> ring[RingD<T>::D];
   Blk<T> b;
   Blk<T> P;
   ScenDev sc;
@@ -612,8 +635,8 @@ __device__ __forceinline__ void warp_copy(void* dst, const void* src, int bytes)
 
 // Stage block `blk`'s descriptor (and its parent's) and scenario counters in the warp's
 // slot, unless they are there already.
-template <class T>
-__device__ __forceinline__ void stage_strip(const KParams<T>& kp, WarpSlot<T>& ws, int blk) {
+template <class T, class WS>
+__device__ __forceinline__ void stage_strip(const KParams<T>& kp, WS& ws, int blk) {
   if (blk == ws.blk) return;
   __syncwarp();
   warp_copy<T>(&ws.b, &RTI_BLK(kp, blk), sizeof(Blk<T>));
@@ -626,17 +649,153 @@ __device__ __forceinline__ void stage_strip(const KParams<T>& kp, WarpSlot<T>& w
   __syncwarp();
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Bounded wait of one warp until child c's patches [u0, u1) x [v0, v1) (parent cells
+// relative to the footprint) hold their means of step s. Patch (u, v) belongs to the
+// strip whose owned columns and rows hold its last cell (3u + 2, 3v + 2), which flags
+// the step once it has ended. Each lane polls the flags of some of those strips with
+// relaxed loads, sleeping between rounds (backing off up to 2 us, so
+// that a waiting warp takes neither issue slots nor L2 bandwidth from the rest). Past
+// `spin_cycles` (lane 0's clock decides for the warp) it flags a timeout in `status` and
+// gives up: the state of the step is then undefined and the host reports the timeout.
+// Each lane's fence after its last poll, then the warp barrier, order the lanes' later
+// loads after the flagged strips' stores.
+template <class T>
+__device__ void wait_child_strips(const KParams<T>& kp, const Blk<T>& c, int u0, int u1,
+                                  int v0, int v1, int s) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x;
+  const int sx0 = (3 * u0 + 2) / kp.tx, sx1 = (3 * (u1 - 1) + 2) / kp.tx;  // inclusive
+  const int sy0 = (3 * v0 + 2) / kp.ty, sy1 = (3 * (v1 - 1) + 2) / kp.ty;
+  const int nxs = sx1 - sx0 + 1, n = nxs * (sy1 - sy0 + 1);
+  const unsigned long long target = ((unsigned long long)s << 32) | kDoneAll;
+  const long long t0 = clock64();
+  unsigned ns = 128;
+  bool gave_up = false;
+  for (int k0 = 0; k0 < n && !gave_up; k0 += 32) {
+    const int k = k0 + lane;
+    const unsigned long long* f = kp.done + c.strip0 + (sy0 + k / nxs) * c.tiles_x + sx0 + k % nxs;
+    bool ok = k >= n || ld_relaxed_u64(f) >= target;
+    while (!__all_sync(full, ok)) {
+      if (__shfl_sync(full, clock64() - t0 > kp.spin_cycles ? 1 : 0, 0)) {
+        if (lane == 0) atomicOr(kp.status, kStTimeout);
+        gave_up = true;
+        break;
+      }
+      __nanosleep(ns);
+      ns = ns < 2048 ? 2 * ns : ns;
+      if (!ok) ok = ld_relaxed_u64(f) >= target;
+    }
+  }
+  __threadfence();
+  __syncwarp();
+}
+
+// A strip has ended step s of the chunk: the warp barrier orders its lanes' stores before
+// lane 0's fence, which orders them before the flag.
+__device__ __forceinline__ void strip_finished(unsigned long long* flag, int s) {
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_relaxed_u64(flag, ((unsigned long long)s << 32) | kDoneAll);
+  }
+}
+
+// The ring strip `td` of a parent with full feedback waits until the means of its region
+// (the rows and columns its march reads) are stored for step s: the child strips that
+// own them come earlier in the work list, and they wait on nothing after them.
+template <class T, class WS>
+__device__ __noinline__ void wait_ring_means(const KParams<T>& kp, const WS& ws, Tile td, int s) {
+  const Blk<T>& b = ws.b;
+  const int ye = min(td.y0 + kp.ty, b.ny);
+  const int c0 = max(td.x0 - 2, 0), c1 = min(td.x0 + kStripW + 2, b.nx);
+  const int r0 = max(td.y0 - 2, 0), r1 = min(ye + 1, b.ny);
+  for (int q = 0; q < b.child_count; ++q) {
+    const Blk<T>& ch = RTI_BLK(kp, RTI_KID(kp, b.child_first + q));
+    const int a0 = ch.i0, a1 = ch.i0 + ch.nx / 3, b0 = ch.j0, b1 = ch.j0 + ch.ny / 3;
+    const int u0 = max(c0, a0) - a0, u1 = min(c1, a1) - a0;
+    const int v0 = max(r0, b0) - b0, v1 = min(r1, b1) - b0;
+    if (u0 < u1 && v0 < v1) wait_child_strips(kp, ch, u0, u1, v0, v1, s);
+  }
+}
+
+// R8 with full feedback, formed by the child's own march (one patch of 3x3 child cells
+// per parent cell). Strip rows r = 3v + 2 with y0 <= r < ye and owned lanes on columns
+// c = 3u + 2 complete patch (u, v): its cells are rows r-2..r (the two records before
+// row r and row r itself) and columns c-2..c (this lane and the two to its left), all of
+// which the strip computes (lanes 0..29 hold correct levels, rows y0-2..ye). Each patch
+// thus belongs to exactly one strip. In binary64 the sum runs in the oracle's order, x
+// outer and y inner: the lane of the patch's first column adds its three wet levels to 0,
+// the next lane continues from that sum, the third from the second's (a dry level adds
+// +0.0, which leaves a sum that is never -0.0 unchanged), and the quotient is the
+// correctly rounded 1/n: the oracle's bits. Binary32 sums each column and then the three
+// column sums (the same terms, associated differently) and takes 1/n from a table of
+// rounded quotients: fewer instructions, and none on the FP64 pipe. The mean over the wet
+// cells, floored at -hP, or "none" goes to the parent's ring plane at (i0 + u, j0 + v).
+// `a0`, `a1`, `a2` are the lane's levels of rows r-2, r-1, r before the block's own ring
+// override, so that every level feeds back what it computed itself.
+static __constant__ float kRecipCount[10] = {0.0f,        1.0f / 1.0f, 1.0f / 2.0f, 1.0f / 3.0f,
+                                             1.0f / 4.0f, 1.0f / 5.0f, 1.0f / 6.0f, 1.0f / 7.0f,
+                                             1.0f / 8.0f, 1.0f / 9.0f};
+
+template <class T>
+__device__ __forceinline__ void patch_means(const Blk<T>& b, const Blk<T>& P, T a0, T h0, T a1,
+                                            T h1, T a2, T h2, bool last, int c, int r) {
+  const unsigned full = 0xffffffffu;
+  const bool w0 = h0 + a0 > b.eps, w1 = h1 + a1 > b.eps, w2 = h2 + a2 > b.eps;
+  const T d0 = w0 ? a0 : T(0), d1 = w1 ? a1 : T(0), d2 = w2 ? a2 : T(0);
+  T acc;
+  if constexpr (sizeof(T) == 8) {
+    acc = ((T(0) + d0) + d1) + d2;                          // the patch's first column
+    acc = ((__shfl_up_sync(full, acc, 1) + d0) + d1) + d2;  // its second
+    acc = ((__shfl_up_sync(full, acc, 1) + d0) + d1) + d2;  // its third: the sum
+  } else {
+    const T col = (d0 + d1) + d2;
+    acc = (__shfl_up_sync(full, col, 2) + __shfl_up_sync(full, col, 1)) + col;
+  }
+  int n = (int)w0 + (int)w1 + (int)w2;
+  n = n + __shfl_up_sync(full, n, 1) + __shfl_up_sync(full, n, 2);
+  if (last) {
+    const size_t o = ix(P, b.i0 + c / 3, b.j0 + r / 3);
+    if (n == 0) {
+      P.ring[o] = ring_none(T(0));
+    } else {
+      T avg;
+      if constexpr (sizeof(T) == 8) avg = acc * (1.0 / (double)n);
+      else avg = acc * kRecipCount[n];
+      const T hP = P.h[o];
+      if (avg < -hP) avg = -hP;
+      P.ring[o] = avg;
+    }
+  }
+}
+
 // Prepass of a strip over the region its march reads: columns x0-2..x0+29, rows
 // y0-2..ye of cells and x-faces, y-faces up to row ye+1. A child's edge faces there get
 // the parent's current fluxes (R7), stored into the child's own level-p arrays, whose
 // edge entries nothing else reads; a parent's ring cells there get their fine-to-coarse
-// eta^{n+1} or "none" (R8) in the ring plane (with full feedback the feedback phase has
-// filled the plane for every covered cell). The items of the region are spread over
+// eta^{n+1} or "none" (R8) in the ring plane, recomputed from the child's level p on the
+// inner ring of each child footprint (with full feedback the children's marches fill the
+// plane for every covered cell: patch_means, wait_ring_means). The items of the region are spread over
 // the lanes; strips that overlap store the same values, and __syncwarp orders the
 // stores before the march's loads. Kept out of line so that the march's registers do
 // not pay for the nesting arithmetic.
-template <class T>
-__device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<T>& ws, Tile td,
+template <class T, class WS>
+__device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WS& ws, Tile td,
                                            int p) {
   const Blk<T>& b = ws.b;
   const int nx = b.nx, ny = b.ny;
@@ -658,7 +817,7 @@ __device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<
       for (int c = c0 + lane; c < c1; c += 32) b.N[p][ix(b, c, g)] = face_n(b, ws.P, p, c, g);
     }
   }
-  if ((td.flags & kTfRing) && !(b.nest & kNestFull)) {  // full feedback: its own phase
+  if ((td.flags & kTfRing) && !(b.nest & kNestFull)) {
     const int c0 = max(cx0, 0), c1 = min(cx1, nx), r0 = max(ry0, 0), r1 = min(ry1, ny);
     for (int q = 0; q < b.child_count; ++q) {
       const Blk<T> ch = RTI_BLK(kp, RTI_KID(kp, b.child_first + q));
@@ -698,9 +857,8 @@ __device__ __noinline__ void strip_prepass(const KParams<T>& kp, const WarpSlot<
 // Step strip td at chunk step s (one warp; ws holds the strip's staged descriptor, the
 // prepass has run). The budget slot of the strip receives sum(eta^{n+1}) and adds the
 // clip, outflow and ring terms.
-template <class T, bool kTrack, bool kLim>
-__device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& ws, Tile td,
-                                            int s) {
+template <class T, bool kTrack, bool kLim, bool kFb, bool kRg, class WS>
+__device__ __forceinline__ void march_strip(const KParams<T>& kp, WS& ws, Tile td, int s) {
   constexpr int kRingD = RingD<T>::D;
   const int lane = threadIdx.x;
   const Blk<T>& b = ws.b;
@@ -729,10 +887,12 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   const int c = td.x0 - 2 + lane;                            // this lane's column (>= -2)
   const bool col_ok = c + kXOff < pitch;                     // inside the allocated row
   const bool own_col = lane >= 2 && lane < 2 + kStripW && c < nx;
+  const bool fb_last = kFb && own_col && (c + 3) % 3 == 2;  // last column of a patch (R8)
   const bool col_x = c >= 1 && c <= nx - 1;  // x-face (c, .) is interior
   const bool col_y = c >= 0 && c <= nx - 1;  // y-face (c, .) lies on a cell column
   const int sl = (lane - 1) & 31, sr = (lane + 1) & 31;  // neighbour bit of a ballot
   const int y0 = td.y0, ye = min(y0 + kp.ty, ny);
+  int fb_ph = (y0 + 1) % 3;  // row r mod 3, from row y0 - 2 (full-feedback march only)
   // this lane's budget partials over the strip's rows (state precision, branch-free
   // adds; the strip's sums are formed and scaled in binary64 at the end)
   T vol_t = T(0), clip_t = T(0), out_t = T(0), ring_t = T(0);
@@ -747,8 +907,9 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   int rowbase = (y0 - 2 + kYOff) * pitch + x0;
   const StageLane SL = stage_lane<T>(lane, x0, pitch);
   for (int k = 0; k < kRingD - 2; ++k) {
-    stage_row<T, kTrack>(ws.ring[k], etaP, hh, Mp, Np, emax, man, vmax, rowbase + k * pitch,
-                         pitch, SL, y0 - 2 + k <= ye);
+    stage_row<T, kTrack>(ws.ring[k], etaP, hh, Mp, Np, emax, man, vmax,
+                         kRg && ring_strip ? b.ring : nullptr, rowbase + k * pitch, pitch, SL,
+                         y0 - 2 + k <= ye);
     cp_async_commit();
   }
   Row<T> A = {}, B = {}, C = {};
@@ -791,8 +952,14 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
     const bool clipped = Nw.H + e < T(0);
     clip_t += (clipped && own) ? -Nw.H - e : T(0);
     e = clipped ? -Nw.H : e;
+    if constexpr (kFb) {  // full feedback: this block's own level, and the patches row r completes
+      ws.fb[fb_ph][lane] = e;  // each lane keeps its own column: no barrier needed
+      if (fb_ph == 2 && r >= y0 && r < ye)
+        patch_means(b, ws.P, ws.fb[0][lane], Y.H, ws.fb[1][lane], Z.H, e, Nw.H, fb_last, c, r);
+      fb_ph = fb_ph == 2 ? 0 : fb_ph + 1;
+    }
     if (ring_strip) {  // fine-to-coarse override (R8), formed by the prepass
-      const T rv = col_ok ? __ldcg(b.ring + o) : ring_none(T(0));
+      const T rv = !col_ok ? ring_none(T(0)) : kRg ? cur.rv : __ldcg(b.ring + o);
       if (!ring_unset(rv) && col_y && rin_x) {
         ring_t += own ? rv - e : T(0);
         e = rv;
@@ -903,15 +1070,19 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
   for (int r = y0 - 2; r <= ye; ++r) {
     // refill the slot of row r - 2: every lane read it before the __syncwarp of row r - 1
     stage_row<T, kTrack>(ws.ring[(slot - 2) & (kRingD - 1)], etaP, hh, Mp, Np, emax, man,
-                         vmax, rowbase + (kRingD - 2) * pitch, pitch, SL,
-                         r + kRingD - 2 <= ye);
+                         vmax, kRg && ring_strip ? b.ring : nullptr,
+                         rowbase + (kRingD - 2) * pitch,
+                         pitch, SL, r + kRingD - 2 <= ye);
     cp_async_commit();
     if (kTrack) cp_async_wait<kRingD - 3>();  // rows r and r + 1 have landed
     else cp_async_wait<kRingD - 2>();         // row r has landed
     __syncwarp();                             // ... for every lane's chunks
     Raw<T> cur = read_row<T, kTrack>(ws.ring[slot], lane);
+    if constexpr (kRg) {
+      if (ring_strip) cur.rv = ws.ring[slot].rg[lane + 2];
+    }
     if (kTrack) {
-      const RingSlot<T>& nx1 = ws.ring[(slot + 1) & (kRingD - 1)];
+      const auto& nx1 = ws.ring[(slot + 1) & (kRingD - 1)];
       cur.eN = nx1.e[lane + 2];
       cur.hN = nx1.h[lane + 2];
     }
@@ -942,11 +1113,6 @@ __device__ __forceinline__ void march_strip(const KParams<T>& kp, WarpSlot<T>& w
 }
 
 // ------------------------------------------------------------------ device-wide barrier
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 // Sense-by-generation barrier over all CTAs of a cooperative launch. The wait is
 // bounded: after spin_cycles the CTA records kStTimeout and every CTA leaves.
@@ -983,134 +1149,50 @@ __device__ __forceinline__ bool grid_barrier(Bar* bar, unsigned& gen, int* statu
 
 // ------------------------------------------------------------------ kernels
 // Steps [s_first, s_first + s_count) of a chunk over every strip of the work list (the
-// kAnyTrack variant also carries the maximum-velocity update, for groups that need it). The
-// warps take strips from a device counter per step (heavy strips come first in the
+// kStepTrack variant also carries the maximum-velocity update, for groups that need it).
+// The warps take strips from a device counter per step (heavy strips come first in the
 // list), so a slow strip delays no fixed set of others. Counter s & 1 serves step s;
 // the other one is cleared during step s, when no warp can still be taking from it
 // (step s - 1 has ended: a barrier or the previous launch lies between). With more than
 // one step the launch must be cooperative: consecutive steps are separated by the
 // device-wide barrier. Variants (kMode): kStepPlain; kStepTrack, whose strips of blocks
-// that keep the maximum velocity take the tracking march; kStepFeedback (cooperative
-// only), which also runs the full-feedback phase of each step, behind one more barrier.
-// A group with full feedback stepped one launch per step runs k_feedback before each
-// kStepPlain or kStepTrack launch instead. The flag kStepLimit added to a variant
-// compiles in the velocity limit (a block without it has vlim = +inf, so its fluxes are
-// unchanged); groups without the limit run variants that do not evaluate it at all.
+// that keep the maximum velocity take the tracking march. The flag kStepLimit added to a
+// variant compiles in the velocity limit (a block without it has vlim = +inf, so its
+// fluxes are unchanged); groups without the limit run variants that do not evaluate it
+// at all. The flag kStepFull compiles in full feedback: the strips of a child with it
+// march with patch_means, which forms the parent's 3x3 means from the levels in
+// registers, and each sets its flag in kp.done once its step has been stored; the
+// parent's ring strips wait for the flags of the child strips under their region
+// (strip_prepass). A flag holds the steps of the chunk its strip has ended (cleared at
+// the chunk's start).
 // Resident CTAs per SM the register allocation targets: binary32 fits 96 registers
-// (5 CTAs of 4 warps) without spilling; binary64 keeps the compiler's choice.
-template <class T>
+// (5 CTAs of 4 warps) with at most a few spilled words; its variants with full feedback
+// or velocity tracking, which spilled 36-100 B at that cap and ran 8-12 % slower, take
+// 128 (4 CTAs); binary64 keeps the compiler's choice.
+template <class T, int kMode>
 struct StepOcc {
   static constexpr int kMinBlocks = 1;
 };
-template <>
-struct StepOcc<float> {
-  static constexpr int kMinBlocks = 5;
+template <int kMode>
+struct StepOcc<float, kMode> {
+  static constexpr int kMinBlocks = (kMode & (kStepFull | kStepTrack)) ? 4 : 5;
 };
 
-// Full-feedback items of step s (R8 on every covered parent cell): items t = w, w + nw,
-// ... of warp w of nw. An item is parent row J, parent cells I0 .. I0 + 31 of one child's
-// footprint: the child's eta^{n+1} on its 3 rows x 96 columns below them, recomputed from
-// its level p with the lanes on consecutive child columns (coalesced loads), go through
-// the warp's ring memory (free in this phase) with their wet flags; then lane k forms
-// the mean of parent cell I0 + k from its 3x3 patch there (binary64, Listing 5 order:
-// x outer, y inner), into the parent's ring plane, which the parent's strips read once
-// the phase has ended. The descriptors go through the warp's slot (parent in ws.b,
-// child in ws.P), which the strip phase stages again.
-template <class T>
-__device__ __noinline__ void feedback_items(const KParams<T>& kp, WarpSlot<T>& ws, int s,
-                                            int w, int nw) {
-  constexpr double kInvWet[10] = {0.0,       1.0 / 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0,
-                                  1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0, 1.0 / 8.0, 1.0 / 9.0};
-  static_assert(sizeof(ws.ring) >= 3 * 96 * (sizeof(T) + 1), "feedback scratch");
-  T* ev = reinterpret_cast<T*>(&ws.ring[0]);                              // [3][96]
-  unsigned char* wf = reinterpret_cast<unsigned char*>(ev + 3 * 96);      // [3][96]
-  const int n = *kp.nfb;
-  const int lane = threadIdx.x;
-  int have_p = -1, have_c = -1;
-  for (int t = w; t < n; t += nw) {
-    const FbItem it = kp.fb[t];
-    if (it.blk != have_p) {
-      __syncwarp();
-      warp_copy<T>(&ws.b, &RTI_BLK(kp, it.blk), sizeof(Blk<T>));
-      have_p = it.blk;
-    }
-    if (it.kid != have_c) {
-      __syncwarp();
-      warp_copy<T>(&ws.P, &RTI_BLK(kp, it.kid), sizeof(Blk<T>));
-      have_c = it.kid;
-    }
-    __syncwarp();
-    const Blk<T>& P = ws.b;
-    const Blk<T>& c = ws.P;
-    const ScenDev sc = kp.scen[P.scen];
-    if ((long long)s >= sc.remaining) continue;  // the scenario has finished
-    const int p = (int)((sc.base + s) & 1);
-    const int ncell = min(32, c.i0 + c.nx / 3 - it.I0);  // parent cells of this item
-    const int x0 = 3 * (it.I0 - c.i0), y0 = 3 * (it.J - c.j0);
-    for (int k = lane; k < 3 * 3 * ncell; k += 32) {  // row-major over 3 rows x 3 ncell cols
-      const int yy = k / (3 * ncell), xx = k - yy * 3 * ncell;
-      const T e = child_eta_next(c, P, p, x0 + xx, y0 + yy);
-      ev[yy * 96 + xx] = e;
-      wf[yy * 96 + xx] = c.h[ix(c, x0 + xx, y0 + yy)] + e > c.eps;
-    }
-    __syncwarp();
-    if (lane < ncell) {
-      double sum = 0.0;
-      int wet = 0;
-      for (int x = 3 * lane; x < 3 * lane + 3; ++x) {  // outer: x (the paper's J)
-        for (int y = 0; y < 3; ++y) {                  // inner: y (the paper's I)
-          if (wf[y * 96 + x]) {
-            sum = sum + (double)ev[y * 96 + x];
-            wet = wet + 1;
-          }
-        }
-      }
-      const size_t o = ix(P, it.I0 + lane, it.J);
-      if (wet == 0) {
-        P.ring[o] = ring_none(T(0));
-      } else {
-        double avg = sum * kInvWet[wet];
-        const double hP = (double)P.h[o];
-        if (avg < -hP) avg = -hP;
-        P.ring[o] = (T)avg;
-      }
-    }
-    __syncwarp();
-  }
-  __syncwarp();
-  if (lane == 0) ws.blk = -1;  // the slot no longer holds a strip's descriptors
-  __syncwarp();
-}
-
-// The full-feedback phase of step s as a launch of its own (one launch per step).
-template <class T>
-__global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
-    k_feedback(KParams<T> kp, int s) {
-  __shared__ WarpSlot<T> slots[kWarps];
-  feedback_items(kp, slots[threadIdx.y], s, blockIdx.x * kWarps + threadIdx.y,
-                 gridDim.x * kWarps);
-}
-
 template <class T, int kMode>
-__global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
+__global__ void __launch_bounds__(kWarps * 32, StepOcc<T, kMode>::kMinBlocks)
     k_step(KParams<T> kp, int s_first, int s_count) {
-  constexpr int kBase = kMode & ~kStepLimit;
-  constexpr bool kLim = (kMode & kStepLimit) != 0;  // some block keeps the velocity limit
-  constexpr bool kAnyTrack = kBase != kStepPlain;
-  __shared__ WarpSlot<T> slots[kWarps];
+  constexpr bool kAnyTrack = (kMode & kStepTrack) != 0;
+  constexpr bool kLim = (kMode & kStepLimit) != 0;      // some block keeps the velocity limit
+  constexpr bool kAnyFull = (kMode & kStepFull) != 0;  // some block has full feedback
+  __shared__ WarpSlot<T, kAnyFull> slots[kWarps];
   __shared__ int go;
-  WarpSlot<T>& ws = slots[threadIdx.y];
+  WarpSlot<T, kAnyFull>& ws = slots[threadIdx.y];
   if (threadIdx.x == 0) ws.blk = -1;
   __syncwarp();
   unsigned gen = 0;
-  if ((kBase == kStepFeedback || s_count > 1) && threadIdx.x == 0 && threadIdx.y == 0)
-    gen = ld_acquire_u32(&kp.bar->gen);
+  if (s_count > 1 && threadIdx.x == 0 && threadIdx.y == 0) gen = ld_acquire_u32(&kp.bar->gen);
   const int nt = *kp.ntiles;
   for (int s = s_first; s < s_first + s_count; ++s) {
-    if (kBase == kStepFeedback) {  // full feedback, then a device-wide barrier
-      feedback_items(kp, ws, s, blockIdx.x * kWarps + threadIdx.y, gridDim.x * kWarps);
-      if (!grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go)) return;
-    }
     if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
       atomicExch(&kp.bar->next[(s + 1) & 1], 0u);
     for (;;) {
@@ -1123,8 +1205,24 @@ __global__ void __launch_bounds__(kWarps * 32, StepOcc<T>::kMinBlocks)
       if ((long long)s >= ws.sc.remaining) continue;  // the scenario has finished
       if ((td.flags & kTfRing) || ws.b.is_child)
         strip_prepass(kp, ws, td, (int)((ws.sc.base + s) & 1));
-      if (kAnyTrack && ws.b.vmax) march_strip<T, true, kLim>(kp, ws, td, s);  // velocity tracked
-      else march_strip<T, false, kLim>(kp, ws, td, s);
+      if constexpr (kAnyFull) {  // a parent's ring strip: its children's means of step s
+        if ((td.flags & kTfRing) && (ws.b.nest & kNestFull)) wait_ring_means(kp, ws, td, s);
+      }
+      const bool fb = kAnyFull && ws.b.is_child && (ws.b.nest & kNestFull);
+      if constexpr (kAnyFull) {  // the ring plane staged (kRg)
+        if (kAnyTrack && ws.b.vmax) {  // velocity tracked
+          if (fb) march_strip<T, true, kLim, true, true>(kp, ws, td, s);
+          else march_strip<T, true, kLim, false, true>(kp, ws, td, s);
+        } else {
+          if (fb) march_strip<T, false, kLim, true, true>(kp, ws, td, s);
+          else march_strip<T, false, kLim, false, true>(kp, ws, td, s);
+        }
+      } else {
+        if (kAnyTrack && ws.b.vmax) march_strip<T, true, kLim, false, false>(kp, ws, td, s);
+        else march_strip<T, false, kLim, false, false>(kp, ws, td, s);
+      }
+      if (fb)
+        strip_finished(kp.done + ws.b.strip0 + (td.y0 / kp.ty) * ws.b.tiles_x + td.x0 / kp.tx, s);
     }
     if (s + 1 < s_first + s_count &&
         !grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go))

@@ -49,6 +49,8 @@ struct Blk {
   int scen;   // scenario slot (ScenDev index)
   int is_child;
   int tiles_x;     // tiles along x (tile slot = ty_index * tiles_x + tx_index)
+  int strip0;      // first of this block's strip flags in the group's flag array (slot
+                   // = strip0 + ty_index * tiles_x + tx_index)
   int nest;        // kNest* bits of the owning handle's nesting options
   double* budget;  // 4 doubles per tile of this block: sum(eta) snapshot, clip, outflow, ring
   int* status;     // the owning handle's device status word
@@ -64,11 +66,15 @@ struct Blk {
 };
 
 // variants of the step kernel
-constexpr int kStepPlain = 0;     // no block keeps the maximum velocity
-constexpr int kStepTrack = 1;     // some block keeps it
-constexpr int kStepFeedback = 2;  // + the full-feedback phase (cooperative launch)
-constexpr int kStepLimit = 4;     // flag added to a variant: some block keeps the velocity limit
-constexpr int kStepModes = 8;     // mode values 0 .. 7 (3 and 7 unused)
+constexpr int kStepPlain = 0;  // no block keeps the maximum velocity
+constexpr int kStepTrack = 1;  // some block keeps it
+constexpr int kStepLimit = 2;  // flag added to a variant: some block keeps the velocity limit
+constexpr int kStepFull = 4;   // flag added to a variant: some block has full feedback
+constexpr int kStepModes = 8;  // mode values 0 .. 7
+
+// Flag of a strip with full feedback: (s << 32) | kDoneAll once the strip has ended step s
+// of the chunk (its patch means stored). Flags only grow within a chunk.
+constexpr unsigned long long kDoneAll = 0xffffffffull;
 
 // nesting options of a block (Blk::nest)
 constexpr int kNestFull = 1;   // fine-to-coarse feedback on every covered parent cell
@@ -90,27 +96,21 @@ struct Tile {
   int blk, x0, y0, flags;
 };
 
-// One item of the full-feedback phase: parent cells (I0 .. I0 + 31, J) inside the
-// footprint of child `kid`, of parent block `blk` (block-table indices).
-struct FbItem {
-  int blk, kid, J, I0;
-};
-
 template <class T>
 struct KParams {
   const Blk<T>* blk;
   const int* kids;
   const Tile* tiles;
   const int* ntiles;   // device-resident tile count (patched between chunks)
-  const FbItem* fb;    // full-feedback items (null when no member uses full feedback)
-  const int* nfb;      // device-resident item count
-  int fb_any;          // the group has full-feedback items (host-known; selects the phase)
+  unsigned long long* done;  // per strip: the last step it has ended (full feedback; kDoneAll)
+  int ndone;                 // entries of `done` (cleared at the start of every chunk)
   ScenDev* scen;
   int* status;         // group status (barrier timeout)
   Bar* bar;
   int nsteps;
   int track;           // some block keeps the maximum velocity (selects the kernel variant)
   int limit;           // some block keeps the velocity limit (selects the kernel variant)
+  int full;            // some block has full feedback (selects the kernel variant)
   int tx, ty;          // tile shape in cells
   long long spin_cycles;
 #ifdef RTI_CHECKED
