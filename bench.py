@@ -35,14 +35,14 @@ SIX_HOURS_STEPS = 108_000  # 6 h at dt = 0.2 s (Sec. V-A)
 # M^{n+1}, N^{n+1}; the rare eta_max / arrival writes are not counted.
 BYTES_PER_CELL_STEP = {"f32": 5 * 4 + 4 + 3 * 4,   # 36
                        "f64": 5 * 8 + 4 + 3 * 8}   # 68
+# cell-steps of FP64 oracle work per host thread the reference arm spreads over its W + K
+# steps (about a minute)
+REF_CELL_STEPS = 0.8e9
 # DRAM bytes per cell-step that ncu measured for k_step<float> (dram__bytes_read.sum +
 # dram__bytes_write.sum of one single-step launch on the 7.95 M-cell 4-level hierarchy,
 # divided by its cells); scaled to a launch of the bench by cells x steps. Set to None
 # whenever the kernel changes until it is captured again.
-# cell-steps of FP64 oracle work per host thread the reference arm spreads over its W + K
-# steps (about a minute)
-REF_CELL_STEPS = 0.8e9
-NCU_F32_DRAM_BYTES_PER_CELL_STEP = (229.257472e6 + 83.613952e6) / 7.95e6  # 39.35 B
+NCU_F32_DRAM_BYTES_PER_CELL_STEP = (229.106432e6 + 82.531328e6) / 7.95e6  # 39.20 B
 
 
 def parse():
