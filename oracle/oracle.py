@@ -92,6 +92,13 @@ def lib(path=None):
             getattr(L, name).argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_cube_root.argtypes = [C.c_double]
         L.orc_cube_root.restype = C.c_double
+        for name in ("orc_phase_mass", "orc_phase_momentum", "orc_phase_edges",
+                     "orc_phase_swap", "orc_means_count", "orc_edge_count"):
+            getattr(L, name).argtypes = [C.c_void_p, C.c_int]
+        for name in ("orc_pack_means", "orc_unpack_means", "orc_get_edge_fluxes",
+                     "orc_set_edge_fluxes"):
+            getattr(L, name).argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc_end_step.argtypes = [C.c_void_p]
         _libs[key] = L
     return _libs[key]
 
@@ -207,6 +214,50 @@ class Oracle:
         out = np.empty(4)
         self._chk(self._L.orc_get_budget(self._s, k, _dptr(out)))
         return dict(volume=out[0], outflow=out[1], clip=out[2], ring=out[3])
+
+    # -- one step in phases, for a hierarchy split over ranks (rti_oracle.h) --
+    def phase_mass(self, k):
+        self._chk(self._L.orc_phase_mass(self._s, k))
+
+    def pack_means(self, k):
+        n = self._L.orc_means_count(self._s, k)
+        if n < 0:
+            raise OracleError(n)
+        out = np.empty(n)
+        self._chk(self._L.orc_pack_means(self._s, k, _dptr(out)))
+        return out
+
+    def unpack_means(self, k, v):
+        v = np.ascontiguousarray(v, np.float64)
+        if v.size != self._L.orc_means_count(self._s, k):
+            raise ValueError("means of the wrong size")
+        self._chk(self._L.orc_unpack_means(self._s, k, _dptr(v)))
+
+    def phase_momentum(self, k):
+        self._chk(self._L.orc_phase_momentum(self._s, k))
+
+    def edge_fluxes(self, k):
+        n = self._L.orc_edge_count(self._s, k)
+        if n < 0:
+            raise OracleError(n)
+        out = np.empty(n)
+        self._chk(self._L.orc_get_edge_fluxes(self._s, k, _dptr(out)))
+        return out
+
+    def set_edge_fluxes(self, k, v):
+        v = np.ascontiguousarray(v, np.float64)
+        if v.size != self._L.orc_edge_count(self._s, k):
+            raise ValueError("edge fluxes of the wrong size")
+        self._chk(self._L.orc_set_edge_fluxes(self._s, k, _dptr(v)))
+
+    def phase_edges(self, k):
+        self._chk(self._L.orc_phase_edges(self._s, k))
+
+    def phase_swap(self, k):
+        self._chk(self._L.orc_phase_swap(self._s, k))
+
+    def end_step(self):
+        self._chk(self._L.orc_end_step(self._s))
 
 
 def cube_root(x):

@@ -700,6 +700,135 @@ int orc_step(orc_state* s, int nsteps) {
 
 long orc_steps_done(const orc_state* s) { return s ? s->step : -1; }
 
+/* ---- one step in phases, for the blocks of one hierarchy split over several ranks ----
+ * orc_step above, taken apart at the points where a block decomposition exchanges data
+ * (Sec. IV-C: the child's means go to the parent after the mass step, the parent's new
+ * fluxes on the footprint edge go to the child after the momentum step). Each rank keeps
+ * a state of the whole hierarchy but steps only its own blocks; the phases below read
+ * and write only the block they are given, except the exchange calls, which move exactly
+ * the values of one message. Called for every block on one rank, in the order the
+ * header gives, they perform orc_step's operations in its order. */
+static int valid_block(const orc_state* s, int k) { return s && k >= 0 && k < s->nb; }
+static int valid_child(const orc_state* s, int k) {
+  return valid_block(s, k) && s->b[k].d.parent >= 0;
+}
+
+int orc_phase_mass(orc_state* s, int k) {
+  if (!valid_block(s, k)) return ORC_ERR_INVALID_ARG;
+  track_speed(&s->b[k], &s->p);
+  mass_block(&s->b[k], &s->p);
+  return ORC_OK;
+}
+
+/* parent cells of child k that receive its mean (its footprint's inner ring, or all of
+ * it with full feedback), in rows J, then columns I */
+int orc_means_count(const orc_state* s, int k) {
+  if (!valid_child(s, k)) return ORC_ERR_INVALID_ARG;
+  int a = s->b[k].nx / 3, bb = s->b[k].ny / 3, n = 0;
+  for (int J = 0; J < bb; ++J)
+    for (int I = 0; I < a; ++I) n += receives(&s->p, I, J, a, bb);
+  return n;
+}
+
+int orc_pack_means(const orc_state* s, int k, double* out) {
+  if (!valid_child(s, k) || !out) return ORC_ERR_INVALID_ARG;
+  int a = s->b[k].nx / 3, bb = s->b[k].ny / 3, n = 0;
+  double* all = (double*)malloc((size_t)a * (size_t)bb * sizeof(double));
+  if (!all) abort();
+  pack_child(s, k, all);
+  for (int J = 0; J < bb; ++J)
+    for (int I = 0; I < a; ++I)
+      if (receives(&s->p, I, J, a, bb)) out[n++] = all[(size_t)J * a + I];
+  free(all);
+  return ORC_OK;
+}
+
+int orc_unpack_means(orc_state* s, int k, const double* in) {
+  if (!valid_child(s, k) || !in) return ORC_ERR_INVALID_ARG;
+  int a = s->b[k].nx / 3, bb = s->b[k].ny / 3, n = 0;
+  double* all = (double*)malloc((size_t)a * (size_t)bb * sizeof(double));
+  if (!all) abort();
+  for (int J = 0; J < bb; ++J)
+    for (int I = 0; I < a; ++I)
+      all[(size_t)J * a + I] = receives(&s->p, I, J, a, bb) ? in[n++] : NAN;
+  unpack_child(s, k, all);
+  free(all);
+  return ORC_OK;
+}
+
+int orc_phase_momentum(orc_state* s, int k) {
+  if (!valid_block(s, k)) return ORC_ERR_INVALID_ARG;
+  oblk* b = &s->b[k];
+  const long nc = (long)b->nx * b->ny;
+  const long step = s->step + 1;
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < nc; ++c) track_cell(b, (size_t)c, step, &s->p);
+  momentum_block(b, &s->p);
+  return ORC_OK;
+}
+
+/* the parent's new fluxes on child k's footprint edge: west and east x-faces over the
+ * footprint's rows, then south and north y-faces over its columns (2 ny/3 + 2 nx/3) */
+int orc_edge_count(const orc_state* s, int k) {
+  if (!valid_child(s, k)) return ORC_ERR_INVALID_ARG;
+  return 2 * (s->b[k].ny / 3) + 2 * (s->b[k].nx / 3);
+}
+
+static void edge_values(orc_state* s, int k, double* v, int set) {
+  const oblk* c = &s->b[k];
+  oblk* P = &s->b[c->d.parent];
+  int a = c->nx / 3, bb = c->ny / 3, i0 = c->d.i0, j0 = c->d.j0, n = 0;
+  for (int side = 0; side < 2; ++side) {
+    int F = side == 0 ? i0 : i0 + a;
+    for (int t = 0; t < bb; ++t, ++n) {
+      double* q = &P->M1[FX(P, F, j0 + t)];
+      if (set) *q = v[n];
+      else v[n] = *q;
+    }
+  }
+  for (int side = 0; side < 2; ++side) {
+    int G = side == 0 ? j0 : j0 + bb;
+    for (int t = 0; t < a; ++t, ++n) {
+      double* q = &P->N1[FY(P, i0 + t, G)];
+      if (set) *q = v[n];
+      else v[n] = *q;
+    }
+  }
+}
+
+int orc_get_edge_fluxes(const orc_state* s, int k, double* out) {
+  if (!valid_child(s, k) || !out) return ORC_ERR_INVALID_ARG;
+  edge_values((orc_state*)s, k, out, 0);
+  return ORC_OK;
+}
+
+int orc_set_edge_fluxes(orc_state* s, int k, const double* in) {
+  if (!valid_child(s, k) || !in) return ORC_ERR_INVALID_ARG;
+  edge_values(s, k, (double*)in, 1);
+  return ORC_OK;
+}
+
+int orc_phase_edges(orc_state* s, int k) {
+  if (!valid_child(s, k)) return ORC_ERR_INVALID_ARG;
+  edges_child(s, k);
+  return ORC_OK;
+}
+
+int orc_phase_swap(orc_state* s, int k) {
+  if (!valid_block(s, k)) return ORC_ERR_INVALID_ARG;
+  oblk* b = &s->b[k];
+  swap_ptr(&b->eta, &b->eta1);
+  swap_ptr(&b->M, &b->M1);
+  swap_ptr(&b->N, &b->N1);
+  return ORC_OK;
+}
+
+int orc_end_step(orc_state* s) {
+  if (!s) return ORC_ERR_INVALID_ARG;
+  s->step += 1;
+  return ORC_OK;
+}
+
 int orc_get_state(const orc_state* s, int k, double* eta, double* M, double* N) {
   if (!s || k < 0 || k >= s->nb) return ORC_ERR_INVALID_ARG;
   const oblk* b = &s->b[k];

@@ -89,6 +89,28 @@ int orc_get_budget(const orc_state* s, int block, double* out);
 /* the cube root the friction term uses (a stated Newton iteration; see rti_oracle.c) */
 double orc_cube_root(double x);
 
+/* One step in phases, for a hierarchy whose blocks are split over several ranks (each
+ * rank holds a state of the whole hierarchy and steps its own blocks). Per step:
+ *   1. orc_phase_mass for each own block;
+ *   2. orc_pack_means for each own child (orc_means_count values) -> the parent's rank;
+ *   3. orc_unpack_means for each child of an own parent, in decreasing block order;
+ *   4. orc_phase_momentum for each own block;
+ *   5. orc_get_edge_fluxes on the parent's rank (orc_edge_count values) -> the child's
+ *      rank, orc_set_edge_fluxes there; orc_phase_edges for each own child;
+ *   6. orc_phase_swap for each own block, orc_end_step once.
+ * On one rank with every block this performs orc_step's operations in its order. */
+int orc_phase_mass(orc_state* s, int block);
+int orc_means_count(const orc_state* s, int child);
+int orc_pack_means(const orc_state* s, int child, double* out);
+int orc_unpack_means(orc_state* s, int child, const double* in);
+int orc_phase_momentum(orc_state* s, int block);
+int orc_edge_count(const orc_state* s, int child);
+int orc_get_edge_fluxes(const orc_state* s, int child, double* out);
+int orc_set_edge_fluxes(orc_state* s, int child, const double* in);
+int orc_phase_edges(orc_state* s, int child);
+int orc_phase_swap(orc_state* s, int block);
+int orc_end_step(orc_state* s);
+
 #ifdef __cplusplus
 }
 #endif
