@@ -8,8 +8,9 @@ request removed from a running batch mid-run leaves the others bitwise unchanged
 
 The wait is made to run out by shortening it (RTI_BARRIER_SPIN_CYCLES, read when a
 handle is created) far below the time one strip takes: the CTAs without a strip reach
-the first barrier at once and give up after about a microsecond. No kernel faults,
-traps or hangs; every CTA leaves by the bounded wait.
+the first barrier at once and give up after about a microsecond. The same limit bounds
+the wait of full feedback's ring strips for their children's strip flags. No kernel
+faults, traps or hangs; every CTA leaves by the bounded wait.
 """
 import os
 import sys
@@ -56,6 +57,38 @@ def test_barrier_wait_runs_out_and_the_handle_recovers(rti, oracle_mod, monkeypa
     h2.sync()
     if precision == 0:
         compare_fp64(h2, o, 1)
+    h2.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_strip_flag_wait_runs_out(rti, oracle_mod, monkeypatch, precision):
+    """Full feedback, one launch per step (no device-wide barrier): a parent's ring strip
+    waits for the flags of the child strips under its region. With the wait shortened
+    far below a strip's duration it gives up, the launch ends, and the next wait reports
+    RTI_ERR_TIMEOUT once; the context stays usable (a handle with the normal wait then
+    matches the oracle)."""
+    sc = S.coastal_hierarchy(
+        "3-level nest, wide child", 9, (200, 120, 810.0), [(1, 216, 135), (1, 135, 90)],
+        dt=0.5, steps=3, shelf_w=15e3, slope_w=20e3, wiggle=2e3, coast_frac=0.6,
+        land_frac=0.4, source=dict(kind="gauss", sigma=8e3, peak=2.0))
+    monkeypatch.setenv("RTI_BARRIER_SPIN_CYCLES", "2000")
+    h = rti.Handle.from_scenario(sc, precision=precision, schedule=rti.SCHED_PER_PASS,
+                                 nest_feedback=rti.NEST_FULL)
+    monkeypatch.delenv("RTI_BARRIER_SPIN_CYCLES")
+    h.step(sc.steps)
+    with pytest.raises(rti.RtiError) as ei:
+        h.sync()
+    assert ei.value.code == -6
+    h.sync()  # reported once: the condition is cleared
+    h.close()
+    h2 = rti.Handle.from_scenario(sc, precision=precision, schedule=rti.SCHED_PER_PASS,
+                                  nest_feedback=rti.NEST_FULL)
+    h2.step(sc.steps)
+    h2.sync()
+    o = oracle_mod.from_scenario(sc, nest_feedback=1)
+    o.step(sc.steps)
+    if precision == 0:
+        compare_fp64(h2, o, 3)
     h2.close()
 
 
