@@ -546,10 +546,8 @@ def run_ours(a):
                           "paper_context": "Kochi 47.2 M cells: 82 s on 32 H100 PCIe, "
                                            "< 2.5 min on 32 Sapphire Rapids CPUs"},
             "e2e": e2e,
-            # per timed rti_step: k_set_scen, the step kernel(s), k_advance; one launch
-            # per step adds k_feedback before each step with full feedback
-            "gpu_launches": 3 if shape["schedule"] == 0 else
-                            a.steps * (2 if a.nest_feedback == "full" else 1) + 2,
+            # per timed rti_step: k_set_scen, the step kernel(s), k_advance
+            "gpu_launches": 3 if shape["schedule"] == 0 else a.steps + 2,
             "serving": srv,
             "autotune": None if not tuned else {
                 "choice": shape, "ms_per_step_short_run": tuned["ms_per_step"],
