@@ -179,8 +179,10 @@ struct Group {
   Tile* d_tiles = nullptr;
   size_t cap_tiles = 0;
   int* d_counts = nullptr;  // [0] = ntiles, [1] = nscen
-  unsigned long long* d_done = nullptr;  // per strip: progress flag (full feedback)
+  unsigned long long* d_done = nullptr;  // per strip: the last step it has ended
   size_t cap_done = 0;      // bytes
+  int* d_dep = nullptr;     // dataflow dependencies: offsets (ntiles + 1), then indices
+  size_t cap_dep = 0;       // bytes
   ScenDev* d_scen = nullptr;
   size_t cap_scen = 0;
   int* d_status = nullptr;
@@ -308,6 +310,7 @@ void free_group_dev(Group* g) {
   cudaFree(g->d_tiles);
   cudaFree(g->d_counts);
   cudaFree(g->d_done);
+  cudaFree(g->d_dep);
   cudaFree(g->d_scen);
   cudaFree(g->d_status);
   cudaFree(g->d_bar);
@@ -319,6 +322,7 @@ void free_group_dev(Group* g) {
   g->d_tiles = nullptr;
   g->d_counts = nullptr;
   g->d_done = nullptr;
+  g->d_dep = nullptr;
   g->d_scen = nullptr;
   g->d_status = nullptr;
   g->d_bar = nullptr;
@@ -363,6 +367,7 @@ KParams<T> kparams(Group* g, int nsteps) {
   kp.ntiles = g->d_counts;
   kp.done = g->d_done;
   kp.ndone = (int)(g->cap_done / sizeof(*g->d_done));
+  kp.dep_off = g->full ? g->d_dep : nullptr;
   kp.scen = g->d_scen;
   kp.status = g->d_status;
   kp.bar = g->d_bar;
@@ -485,6 +490,69 @@ std::vector<Tile> full_feedback_order(const std::vector<Blk<T>>& blks,
   return out;
 }
 
+// Dependencies of the steps of a chunk run as one dataflow (no device-wide barrier):
+// strip X's step s may start once these strips (as flag indices, strip0 + slot) have
+// ended step s - 1. A strip reads, at step s, cells and faces up to 4 columns and 2 rows
+// beyond its own (its 3 x 3 neighbourhood of strips, itself included, wrote them at step
+// s - 1) and overwrites at step s what they read at step s - 1 (the ping-pong buffers).
+// Across levels the conservative rule: a child strip and a parent strip depend on each
+// other both ways when the child strip's region, in parent cells and one cell wider,
+// meets the parent strip's region (the child pulls the parent's edge fluxes, the
+// parent's ring strip recomputes or reads the child's levels, and each overwrites at the
+// next step what the other read). Returns CSR lists by work-list position: deps of list
+// entry t are idx[off[t] .. off[t+1]).
+template <class T>
+void dataflow_deps(const std::vector<Blk<T>>& blks, const std::vector<Tile>& tiles, int tx,
+                   int ty, std::vector<int>* off, std::vector<int>* idx) {
+  const int n = (int)tiles.size();
+  std::vector<std::vector<int>> deps(n);
+  std::vector<int> pos;  // flag index -> work-list position
+  for (const Blk<T>& b : blks) pos.resize(std::max<size_t>(pos.size(), (size_t)b.strip0 +
+                                                            b.tiles_x * ((b.ny + ty - 1) / ty)));
+  auto flag_of = [&](const Tile& t) {
+    const Blk<T>& b = blks[t.blk];
+    return b.strip0 + (t.y0 / ty) * b.tiles_x + t.x0 / tx;
+  };
+  for (int t = 0; t < n; ++t) pos[flag_of(tiles[t])] = t;
+  auto floor_div = [](int a, int d) { return a >= 0 ? a / d : -((-a + d - 1) / d); };
+  for (int t = 0; t < n; ++t) {
+    const Tile& td = tiles[t];
+    const Blk<T>& b = blks[td.blk];
+    const int tiles_y = (b.ny + ty - 1) / ty, sx = td.x0 / tx, sy = td.y0 / ty;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x = sx + dx, y = sy + dy;
+        if (x >= 0 && x < b.tiles_x && y >= 0 && y < tiles_y)
+          deps[t].push_back(b.strip0 + y * b.tiles_x + x);
+      }
+    if (!b.is_child) continue;
+    // this child strip's region in parent cells, one cell wider
+    const Blk<T>& P = blks[b.parent];
+    const int ye = std::min(td.y0 + ty, b.ny);
+    const int pc0 = b.i0 + floor_div(td.x0 - 4, 3) - 1, pc1 = b.i0 + (td.x0 + tx + 4 + 2) / 3 + 1;
+    const int pr0 = b.j0 + floor_div(td.y0 - 2, 3) - 1, pr1 = b.j0 + (ye + 2 + 2) / 3 + 1;
+    const int ptiles_y = (P.ny + ty - 1) / ty;
+    for (int y = std::max(0, floor_div(pr0 - ty - 2, ty)); y < ptiles_y && y * ty - 2 < pr1; ++y)
+      for (int x = std::max(0, floor_div(pc0 - tx - 4, tx)); x < P.tiles_x && x * tx - 4 < pc1;
+           ++x) {
+        const int px0 = x * tx - 4, px1 = x * tx + tx + 4;
+        const int py0 = y * ty - 2, py1 = std::min(y * ty + ty, P.ny) + 2;
+        if (px0 >= pc1 || pc0 >= px1 || py0 >= pr1 || pr0 >= py1) continue;
+        const int pf = P.strip0 + y * P.tiles_x + x;
+        deps[t].push_back(pf);                     // the child strip waits on the parent's
+        deps[pos[pf]].push_back(flag_of(td));      // and the parent strip on the child's
+      }
+  }
+  off->assign(1, 0);
+  idx->clear();
+  for (int t = 0; t < n; ++t) {
+    std::sort(deps[t].begin(), deps[t].end());
+    deps[t].erase(std::unique(deps[t].begin(), deps[t].end()), deps[t].end());
+    idx->insert(idx->end(), deps[t].begin(), deps[t].end());
+    off->push_back((int)idx->size());
+  }
+}
+
 // Rebuild and upload the block table, child lists and tile list of a group (stream-ordered).
 template <class T>
 int group_upload(Group* g, cudaStream_t st, std::string* err) {
@@ -569,6 +637,8 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
       grid = g->grid;
     tiles = full_feedback_order<T>(blks, kids, tiles, g->tx, g->ty, grid * kWarps);
   }
+  std::vector<int> dep_off, dep_idx;  // the dataflow of full-feedback chunks
+  if (full_any) dataflow_deps<T>(blks, tiles, g->tx, g->ty, &dep_off, &dep_idx);
   bool moved = false;
   cudaError_t e = grow(&g->d_blk, &g->cap_blk, blks.size() * sizeof(Blk<T>) + 64, &moved);
   if (e == cudaSuccess) e = grow(&g->d_kids, &g->cap_kids, kids.size() * sizeof(int) + 64, &moved);
@@ -577,6 +647,8 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
     e = grow(&g->d_scen, &g->cap_scen, g->members.size() * sizeof(ScenDev) + 64, &moved);
   if (e == cudaSuccess)
     e = grow(&g->d_done, &g->cap_done, (size_t)nflags * sizeof(*g->d_done), &moved);
+  if (e == cudaSuccess)
+    e = grow(&g->d_dep, &g->cap_dep, (dep_off.size() + dep_idx.size()) * sizeof(int), &moved);
   if (e != cudaSuccess) return cuda_err(err, e, "device tables");
   // the captured graph holds the old pointers and sizes, or the other kernel variant
   if ((moved || track != g->track || limit != g->limit || full_any != g->full) && g->gexec) {
@@ -588,8 +660,9 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   const size_t nb_kids = kids.size() * sizeof(int);
   const size_t nb_tiles = tiles.size() * sizeof(Tile);
   const size_t nb_scen = g->members.size() * sizeof(ScenDev);
+  const size_t nb_dep = (dep_off.size() + dep_idx.size()) * sizeof(int);
   const size_t need = align256(nb_blk) + align256(nb_kids) + align256(nb_tiles) +
-                      align256(nb_scen) + 256;
+                      align256(nb_scen) + align256(nb_dep) + 256;
   // the previous upload must have left the staging buffer before it is rewritten
   e = cudaEventSynchronize(g->staged);
   if (e != cudaSuccess) return cuda_err(err, e, "staging wait");
@@ -619,6 +692,9 @@ int group_upload(Group* g, cudaStream_t st, std::string* err) {
   if (e == cudaSuccess) e = put(kids.data(), nb_kids, g->d_kids);
   if (e == cudaSuccess) e = put(tiles.data(), nb_tiles, g->d_tiles);
   if (e == cudaSuccess) e = put(sc.data(), nb_scen, g->d_scen);
+  std::vector<int> dep(dep_off);
+  dep.insert(dep.end(), dep_idx.begin(), dep_idx.end());
+  if (e == cudaSuccess) e = put(dep.data(), nb_dep, g->d_dep);
   if (e == cudaSuccess) e = put(counts, sizeof(counts), g->d_counts);
   if (e == cudaSuccess) e = cudaEventRecord(g->staged, st);
   if (e != cudaSuccess) return cuda_err(err, e, "table upload");

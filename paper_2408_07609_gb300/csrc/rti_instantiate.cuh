@@ -6,7 +6,7 @@ namespace rti {
 
 namespace {
 // the step kernel of variant `mode` (kStepPlain or kStepTrack, plus kStepLimit and
-// kStepFull)
+// kStepFull; the full-feedback variants are k_step_flow)
 using StepFn = void (*)(KParams<RTI_T>, int, int);
 StepFn step_kernel(int mode) {
   switch (mode) {
@@ -14,10 +14,10 @@ StepFn step_kernel(int mode) {
     case 1: return k_step<RTI_T, 1>;
     case 2: return k_step<RTI_T, 2>;
     case 3: return k_step<RTI_T, 3>;
-    case 4: return k_step<RTI_T, 4>;
-    case 5: return k_step<RTI_T, 5>;
-    case 6: return k_step<RTI_T, 6>;
-    case 7: return k_step<RTI_T, 7>;
+    case 4: return k_step_flow<RTI_T, 4>;
+    case 5: return k_step_flow<RTI_T, 5>;
+    case 6: return k_step_flow<RTI_T, 6>;
+    case 7: return k_step_flow<RTI_T, 7>;
     default: return nullptr;
   }
 }

@@ -664,6 +664,37 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Bounded wait of one warp until the flags kp.done[list[0 .. n)] reach `target` (lanes
+// poll some each, relaxed loads, sleeping between rounds up to 2 us; past spin_cycles the
+// warp flags a timeout and gives up). Each lane's fence after its last poll, then the
+// warp barrier, order the lanes' later loads after the flagged strips' stores.
+template <class T>
+__device__ __noinline__ void wait_flags(const KParams<T>& kp, const int* list, int n,
+                                        unsigned long long target) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x;
+  const long long t0 = clock64();
+  unsigned ns = 64;
+  bool gave_up = false;
+  for (int k0 = 0; k0 < n && !gave_up; k0 += 32) {
+    const int k = k0 + lane;
+    const unsigned long long* f = k < n ? kp.done + list[k] : nullptr;
+    bool ok = !f || ld_relaxed_u64(f) >= target;
+    while (!__all_sync(full, ok)) {
+      if (__shfl_sync(full, clock64() - t0 > kp.spin_cycles ? 1 : 0, 0)) {
+        if (lane == 0) atomicOr(kp.status, kStTimeout);
+        gave_up = true;
+        break;
+      }
+      __nanosleep(ns);
+      ns = ns < 2048 ? 2 * ns : ns;
+      if (!ok) ok = ld_relaxed_u64(f) >= target;
+    }
+  }
+  __threadfence();
+  __syncwarp();
+}
+
 // Bounded wait of one warp until child c's patches [u0, u1) x [v0, v1) (parent cells
 // relative to the footprint) hold their means of step s. Patch (u, v) belongs to the
 // strip whose owned columns and rows hold its last cell (3u + 2, 3v + 2), which flags
@@ -1159,12 +1190,15 @@ __device__ __forceinline__ bool grid_barrier(Bar* bar, unsigned& gen, int* statu
 // that keep the maximum velocity take the tracking march. The flag kStepLimit added to a
 // variant compiles in the velocity limit (a block without it has vlim = +inf, so its
 // fluxes are unchanged); groups without the limit run variants that do not evaluate it
-// at all. The flag kStepFull compiles in full feedback: the strips of a child with it
-// march with patch_means, which forms the parent's 3x3 means from the levels in
-// registers, and each sets its flag in kp.done once its step has been stored; the
-// parent's ring strips wait for the flags of the child strips under their region
-// (strip_prepass). A flag holds the steps of the chunk its strip has ended (cleared at
-// the chunk's start).
+// at all. The flag kStepFull selects k_step_flow, which compiles in full feedback: the
+// strips of a child with it march with patch_means, which forms the parent's 3x3 means
+// from the levels in registers, and each sets its flag in kp.done once its step has been
+// stored; the parent's ring strips wait for the flags of the child strips under their
+// region (wait_ring_means). A flag holds the last step of the chunk its strip has ended
+// (cleared at the chunk's start). With more than one step k_step_flow runs the chunk as
+// one dataflow: every strip sets its flag, and a strip's next step waits only for the
+// strips it depends on (the host's lists, dataflow_deps) instead of a device-wide
+// barrier, so the end of one step overlaps the start of the next.
 // Resident CTAs per SM the register allocation targets: binary32 fits 96 registers
 // (5 CTAs of 4 warps) with at most a few spilled words; its variants with full feedback
 // or velocity tracking, which spilled 36-100 B at that cap and ran 8-12 % slower, take
@@ -1178,15 +1212,52 @@ struct StepOcc<float, kMode> {
   static constexpr int kMinBlocks = (kMode & (kStepFull | kStepTrack)) ? 4 : 5;
 };
 
+// One strip t at chunk step s: its prepass, its full-feedback wait, its march, and its
+// flag where a strip waits on it (full feedback, or the dataflow `df` of a full-feedback
+// group, where it first waits for the strips it depends on to end step s - 1).
+template <class T, int kMode, class WS>
+__device__ __forceinline__ void strip_step(const KParams<T>& kp, WS& ws, int t, int s,
+                                           int s_first, bool df, const int* dep_idx) {
+  constexpr bool kAnyTrack = (kMode & kStepTrack) != 0;
+  constexpr bool kLim = (kMode & kStepLimit) != 0;
+  constexpr bool kAnyFull = (kMode & kStepFull) != 0;
+  const Tile td = kp.tiles[t];
+  stage_strip(kp, ws, td.blk);
+  if ((long long)s >= ws.sc.remaining) return;  // the scenario has finished
+  if constexpr (kAnyFull) {
+    if (df && s > s_first)  // the strips this one depends on have ended step s - 1
+      wait_flags(kp, dep_idx + kp.dep_off[t], kp.dep_off[t + 1] - kp.dep_off[t],
+                 ((unsigned long long)(s - 1) << 32) | kDoneAll);
+  }
+  if ((td.flags & kTfRing) || ws.b.is_child)
+    strip_prepass(kp, ws, td, (int)((ws.sc.base + s) & 1));
+  if constexpr (kAnyFull) {  // a parent's ring strip: its children's means of step s
+    if ((td.flags & kTfRing) && (ws.b.nest & kNestFull)) wait_ring_means(kp, ws, td, s);
+    const bool fb = ws.b.is_child && (ws.b.nest & kNestFull);
+    if (kAnyTrack && ws.b.vmax) {  // velocity tracked; the ring plane staged (kRg)
+      if (fb) march_strip<T, true, kLim, true, true>(kp, ws, td, s);
+      else march_strip<T, true, kLim, false, true>(kp, ws, td, s);
+    } else {
+      if (fb) march_strip<T, false, kLim, true, true>(kp, ws, td, s);
+      else march_strip<T, false, kLim, false, true>(kp, ws, td, s);
+    }
+    if (fb || df)
+      strip_finished(kp.done + ws.b.strip0 + (td.y0 / kp.ty) * ws.b.tiles_x + td.x0 / kp.tx, s);
+  } else {
+    if (kAnyTrack && ws.b.vmax) march_strip<T, true, kLim, false, false>(kp, ws, td, s);
+    else march_strip<T, false, kLim, false, false>(kp, ws, td, s);
+  }
+}
+
 template <class T, int kMode>
 __global__ void __launch_bounds__(kWarps * 32, StepOcc<T, kMode>::kMinBlocks)
     k_step(KParams<T> kp, int s_first, int s_count) {
   constexpr bool kAnyTrack = (kMode & kStepTrack) != 0;
-  constexpr bool kLim = (kMode & kStepLimit) != 0;      // some block keeps the velocity limit
-  constexpr bool kAnyFull = (kMode & kStepFull) != 0;  // some block has full feedback
-  __shared__ WarpSlot<T, kAnyFull> slots[kWarps];
+  constexpr bool kLim = (kMode & kStepLimit) != 0;  // some block keeps the velocity limit
+  static_assert((kMode & kStepFull) == 0, "the full-feedback variants run k_step_flow");
+  __shared__ WarpSlot<T, false> slots[kWarps];
   __shared__ int go;
-  WarpSlot<T, kAnyFull>& ws = slots[threadIdx.y];
+  WarpSlot<T, false>& ws = slots[threadIdx.y];
   if (threadIdx.x == 0) ws.blk = -1;
   __syncwarp();
   unsigned gen = 0;
@@ -1205,28 +1276,63 @@ __global__ void __launch_bounds__(kWarps * 32, StepOcc<T, kMode>::kMinBlocks)
       if ((long long)s >= ws.sc.remaining) continue;  // the scenario has finished
       if ((td.flags & kTfRing) || ws.b.is_child)
         strip_prepass(kp, ws, td, (int)((ws.sc.base + s) & 1));
-      if constexpr (kAnyFull) {  // a parent's ring strip: its children's means of step s
-        if ((td.flags & kTfRing) && (ws.b.nest & kNestFull)) wait_ring_means(kp, ws, td, s);
-      }
-      const bool fb = kAnyFull && ws.b.is_child && (ws.b.nest & kNestFull);
-      if constexpr (kAnyFull) {  // the ring plane staged (kRg)
-        if (kAnyTrack && ws.b.vmax) {  // velocity tracked
-          if (fb) march_strip<T, true, kLim, true, true>(kp, ws, td, s);
-          else march_strip<T, true, kLim, false, true>(kp, ws, td, s);
-        } else {
-          if (fb) march_strip<T, false, kLim, true, true>(kp, ws, td, s);
-          else march_strip<T, false, kLim, false, true>(kp, ws, td, s);
-        }
-      } else {
-        if (kAnyTrack && ws.b.vmax) march_strip<T, true, kLim, false, false>(kp, ws, td, s);
-        else march_strip<T, false, kLim, false, false>(kp, ws, td, s);
-      }
-      if (fb)
-        strip_finished(kp.done + ws.b.strip0 + (td.y0 / kp.ty) * ws.b.tiles_x + td.x0 / kp.tx, s);
+      if (kAnyTrack && ws.b.vmax) march_strip<T, true, kLim, false, false>(kp, ws, td, s);
+      else march_strip<T, false, kLim, false, false>(kp, ws, td, s);
     }
     if (s + 1 < s_first + s_count &&
         !grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go))
       return;
+  }
+}
+
+// The step kernel of full-feedback groups (kMode has kStepFull): the same strips, but a
+// chunk runs as one dataflow when its dependency lists are given (kp.dep_off).
+template <class T, int kMode>
+__global__ void __launch_bounds__(kWarps * 32, StepOcc<T, kMode>::kMinBlocks)
+    k_step_flow(KParams<T> kp, int s_first, int s_count) {
+  static_assert((kMode & kStepFull) != 0, "the full-feedback variants");
+  __shared__ WarpSlot<T, true> slots[kWarps];
+  __shared__ int go;
+  WarpSlot<T, true>& ws = slots[threadIdx.y];
+  if (threadIdx.x == 0) ws.blk = -1;
+  __syncwarp();
+  const int nt = *kp.ntiles;
+  unsigned gen = 0;
+  {
+    // A chunk of a full-feedback group runs as one dataflow: its steps x strips in one
+    // sequence, each strip starting once the strips it depends on have ended the previous
+    // step (no device-wide barrier, so a step's end overlaps the next step's start).
+    const bool df = kp.dep_off && s_count > 1 &&
+                    (unsigned long long)s_count * (unsigned long long)nt < 0xff000000ull;
+    const unsigned total = df ? (unsigned)s_count * (unsigned)nt : 0u;
+    const int* dep_idx = df ? kp.dep_off + nt + 1 : nullptr;
+    if (!df && s_count > 1 && threadIdx.x == 0 && threadIdx.y == 0)
+      gen = ld_acquire_u32(&kp.bar->gen);
+    int s = s_first;
+    if (!df && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+      atomicExch(&kp.bar->next[(s + 1) & 1], 0u);
+    for (;;) {
+      unsigned i = 0;
+      if (threadIdx.x == 0) i = atomicAdd(&kp.bar->next[df ? 0 : (s & 1)], 1u);
+      i = __shfl_sync(0xffffffffu, i, 0);
+      int t;
+      if (df) {
+        if (i >= total) break;
+        s = s_first + (int)(i / (unsigned)nt);
+        t = (int)(i % (unsigned)nt);
+      } else {
+        if (i >= (unsigned)nt) {  // this step's strips are all taken
+          if (s + 1 >= s_first + s_count) break;
+          if (!grid_barrier(kp.bar, gen, kp.status, kp.spin_cycles, &go)) return;
+          ++s;
+          if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+            atomicExch(&kp.bar->next[(s + 1) & 1], 0u);
+          continue;
+        }
+        t = (int)i;
+      }
+      strip_step<T, kMode>(kp, ws, t, s, s_first, df, dep_idx);
+    }
   }
 }
 

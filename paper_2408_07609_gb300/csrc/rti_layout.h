@@ -102,8 +102,11 @@ struct KParams {
   const int* kids;
   const Tile* tiles;
   const int* ntiles;   // device-resident tile count (patched between chunks)
-  unsigned long long* done;  // per strip: the last step it has ended (full feedback; kDoneAll)
+  unsigned long long* done;  // per strip: the last step it has ended (kDoneAll)
   int ndone;                 // entries of `done` (cleared at the start of every chunk)
+  const int* dep_off;        // dataflow: strips (flag indices) work-list entry t waits on at
+                             // its previous step are idx[dep_off[t] .. dep_off[t+1]), with
+                             // idx = dep_off + ntiles + 1; null: steps separated by barriers
   ScenDev* scen;
   int* status;         // group status (barrier timeout)
   Bar* bar;
