@@ -37,9 +37,11 @@ extern "C" {
 #define RTI_ERR_NESTING -3     /* child not 1:3, not inside its parent with a 3-cell margin, overlapping siblings, parents not listed first */
 #define RTI_ERR_OOM -4         /* device memory exhausted or caller arena too small */
 #define RTI_ERR_NONFINITE -5   /* a non-finite water level appeared on the device */
-#define RTI_ERR_TIMEOUT -6     /* a device-wide barrier wait ran out; the state is undefined until
-                                  rti_set_initial_uplift or rti_set_state sets it again (the
-                                  condition is cleared when it is reported) */
+#define RTI_ERR_TIMEOUT -6     /* a bounded device wait ran out (the device-wide barrier between
+                                  steps, or a strip's wait for the strips it depends on); the
+                                  state is undefined until rti_set_initial_uplift or
+                                  rti_set_state sets it again (the condition is cleared when
+                                  it is reported) */
 #define RTI_ERR_CUDA -7        /* a CUDA runtime call failed (message in rti_last_error) */
 #define RTI_ERR_STATE -8       /* call not allowed in the current state (e.g. handle in a batch) */
 
@@ -61,7 +63,9 @@ extern "C" {
 #define RTI_FLUX_CONSTANT 1 /* each fine face takes its coarse face's flux (the edge carries
                                exactly the coarse discharge) */
 
-#define RTI_SCHED_PERSISTENT 0 /* one cooperative launch per chunk of steps, device-wide barriers */
+#define RTI_SCHED_PERSISTENT 0 /* one cooperative launch per chunk of steps: device-wide barriers
+                                  between steps, or with full feedback one dataflow in which
+                                  each strip waits only for the strips it depends on */
 #define RTI_SCHED_PER_PASS 1   /* one ordinary launch per step (no device-wide barrier) */
 
 /* One rectangular block of a grid level (Sec. II-A "blocks"). */
@@ -126,8 +130,8 @@ int rti_set_initial_uplift(rti_handle* h, int block, const double* dz);
  * the legacy default stream) and return without waiting. One step is the time-integration
  * loop body of Sec. IV-A / Fig. 2 on every block with one dt (Sec. V-A): mass (Eq. 1),
  * fine-to-coarse level (Sec. IV-C-2, Listing 5), momentum (Eqs. 2-3), coarse-to-fine
- * fluxes, output update, buffer swap. Device errors (non-finite level, barrier timeout)
- * are reported by the next call that waits. */
+ * fluxes, output update, buffer swap. Device errors (non-finite level, a bounded wait
+ * that ran out) are reported by the next call that waits. */
 int rti_step(rti_handle* h, int nsteps, void* stream);
 
 /* Wait for the handle's enqueued work and return its device status. */
