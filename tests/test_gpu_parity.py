@@ -1,7 +1,8 @@
 """CUDA path vs the FP64 oracle, element by element, on seeded synthetic inputs.
 
 Binary64 bar: max|gpu - oracle| / max|oracle| <= 1e-12 per field and block (the
-kernels round like the oracle; only the library cbrt may differ by an ulp).
+kernels perform the oracle's operations in its order, the cube root included, so the
+states agree bit for bit; the bar leaves room for the budget sums' order).
 Binary32 bar: the accuracy stated for the forecast outputs (max |d eta| in metres,
 wet/dry mismatch, arrival error); see test_fp32_accuracy_report.
 """
