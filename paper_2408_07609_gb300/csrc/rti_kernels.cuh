@@ -248,10 +248,11 @@ __device__ __forceinline__ T upwind(T w, T phim, T phi0, T phip, bool okm, bool 
 
 // Arithmetic of the momentum update in the state precision. Binary64 keeps the oracle's
 // exact expressions (correctly rounded divide and square root, the stated cube-root
-// iteration cube_root_nr) so that it reproduces the oracle's rounding bit for bit. Binary32 (the forecast path, checked against the
-// oracle within the stated accuracy) uses the special-function unit: approximate
-// reciprocals, and sqrt(M^2 + N^2) D^(-7/3) = 2^(log2(M^2 + N^2)/2 - 7/3 log2 D) with
-// the PTX lg2.approx / ex2.approx instructions (log2 0 = -inf gives a zero friction).
+// iteration cube_root_nr) so that it reproduces the oracle's rounding bit for bit.
+// Binary32 (the forecast path, checked against the oracle within the stated accuracy)
+// uses the special-function unit: approximate reciprocals, and sqrt(M^2 + N^2) D^(-7/3)
+// = 2^(log2(M^2 + N^2)/2 - 7/3 log2 D) with the PTX lg2.approx / ex2.approx instructions
+// (log2 0 = -inf gives a zero friction).
 __device__ __forceinline__ float lg2_approx(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
