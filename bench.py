@@ -81,6 +81,8 @@ def parse():
                     help="compare FP32 with FP64 on the 46.65 M-cell workload over N steps "
                          "(0: skip)")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-latency", action="store_true",
+                    help="skip the small configurations' time per step")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default launch shape (28 x 64 strips, all CTAs that fit, "
                          "persistent) instead of the autotuner's choice")
@@ -448,6 +450,21 @@ def accuracy(rti, sc=None, steps=None):
             "arrival_mismatch_cells": arr_mis}
 
 
+def latency(rti, steps=200, warmup=5):
+    """Time per step of the small configurations, which fit in L2 (so latency, not a
+    roofline): the 256 x 256 single grid and the 3-level 765 k-cell nest, each precision,
+    one persistent launch of `steps` (the nest: steps / 2) after `warmup`."""
+    from paper_2408_07609_gb300 import scenarios as S
+
+    out = {}
+    for name, sc, n in (("single_grid_256x256", S.config1(steps=0), steps),
+                        ("nest_3level_765k", S.config2(steps=0), steps // 2)):
+        for prec, label in ((rti.FP32, "fp32"), (rti.FP64, "fp64")):
+            ms = time_device(rti, sc, prec, n, warmup, 0, 1)
+            out[f"{name}_{label}_us_per_step"] = 1e3 * ms / n
+    return out
+
+
 def cpu_baseline(sc, steps, parallel):
     """The FP64 oracle, as it stands, on the host: a bounded sample of the workload, in
     its OpenMP build over every host core (parallel) or single-threaded. Returns the
@@ -511,6 +528,7 @@ def run_ours(a):
     acc = None if (a.no_accuracy or rank != 0) else accuracy(rti)
     acc4 = None if (not a.accuracy_c4_steps or rank != 0) else accuracy(rti, sc, a.accuracy_c4_steps)
     c3 = None if a.no_batch else batch_c3(rti, tune=not a.no_autotune, cache=a.tune_cache)
+    lat = None if (a.no_latency or rank != 0 or world != 1) else latency(rti)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         dt, cores = cpu_baseline(sc, a.cpu_steps, parallel=True)
@@ -557,6 +575,7 @@ def run_ours(a):
             "fp32_accuracy": acc,
             "fp32_accuracy_c4": acc4,
             "batch_c3": c3,
+            "latency_small": lat,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": (None if NCU_F32_DRAM_BYTES_PER_CELL_STEP is None
@@ -566,7 +585,8 @@ def run_ours(a):
                                          "a single-step ncu capture of the 4-level case",
                          "peak_kind": f"{kind} hbm_gbs",
                          "bytes_per_cell_step": bpc,
-                         "kernel": f"k_step<float, {'true' if a.track_velocity else 'false'}>"},
+                         "kernel": ("k_step_flow" if a.nest_feedback == "full" else "k_step")
+                                   + f"<float, {(1 if a.track_velocity else 0) | (4 if a.nest_feedback == 'full' else 0)}>"},
             "cpu_baseline": cpu,
             "clocks": clocks,
         })
